@@ -1,0 +1,503 @@
+"""Plain, slow, FP64 reference of one Elfpie iteration (arXiv 2209.14671).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline legs, never by the CUDA product path.
+
+Everything is complex128 / float64 NumPy, one operation per line, in the order of
+Algorithm 1 (Sec. 3.4).  The paper leaves several points silent or garbled; the
+readings taken here are labelled A1..A16 and listed with their reasons in the
+design notes of the repository.  In short:
+
+* A1  transforms: Psi = fftshift(DFT_N(O)), O = IDFT_N(ifftshift(Psi)) (IDFT
+      carries 1/A); o_n = u^-2 IDFT_n(ifftshift(P o C_n Psi)).  Sec. 3.1, Eqs. 1, 6.
+* A3  LED offset c_n = round-half-away-from-zero(k_n / dk), dk = 1/(n dx).
+* A4  pupil support S = {|j - n/2|^2 dk^2 <= (NA/lambda)^2}.
+* A5  nabla = forward differences with a Neumann (zero) last row/column.
+* A6  H = (Dxx, Dyy, sqrt2 Dxy) on the valid interior [1, N-2]^2.
+* A7  the L1 "gradient 0 at the origin" rule (Sec. 3.3) is a Huber smoothing:
+      phi(x) = |x| for |x| >= tau, |x|^2/(2 tau) + tau/2 below.
+* A8  Eq. 11's residual is model minus measured in the intensity domain.
+* A9  initial state: Psi0 from the centre-LED image, mu = v = 0, delta = s0^2.
+* A10 alpha (Eq. 16): 'valid' 3x3 correlation, mean over the (n-2)^2 interior.
+* A11 every gradient is the true dL/d(conj z) (Eq. 10's missing 1/2 restored).
+* A12 phase = atan2 without unwrapping.  A13 eta_H = 1e-12.  A14 eta_opt = 1e-8.
+* A15 pupil: P~ = G3 (x) P, P_new = mask o (P~ - Delta_P), gradient at P^t.
+* A16 s0_P = 1e-2.
+
+Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
+(brute-force DFT, Parseval, adjoint identities, finite differences, affine null
+space of H, closed forms for alpha and the first AdaBelief step, noiseless
+convergence).  The reconstruction-quality numbers of the paper's Tables 2-4 are
+parity unpinned (their images and comparison codes are not available).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Options", "Geometry", "State", "round_half_away", "make_geometry",
+    "crop", "crop_adjoint", "forward_field", "forward_intensity",
+    "grad_op", "grad_adj", "huber", "hessian_op", "hessian_adj",
+    "fidelity_cost_grad", "object_from_spectrum", "spectrum_from_object",
+    "hessian_cost_grad", "adabelief", "gauss3", "filter3", "alpha_estimate",
+    "init_state", "iteration", "run", "total_cost", "centre_led",
+    "LAPLACE_KERNEL",
+]
+
+
+# ----------------------------------------------------------------------------
+# options and geometry
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Options:
+    """Hyper-parameters of Sec. 6.2 and the smoothing constants of the readings.
+
+    fidelity: 0 = intensity (Eq. 5, default), 1 = amplitude (Eq. 4).
+    omega_iso: 1 = isotropic normaliser (Eq. 12 first case), 0 = anisotropic.
+    alpha/beta < 0 select the automatic estimate of Eqs. 16-17.
+    gamma1, gamma2: the r1, r2 of Sec. 6.2 (0.9 / 0.999).
+    s0_psi, s0_pupil: initial step sqrt(delta^0) of Eq. 19 for Psi and P.
+    """
+    fidelity: int = 0
+    omega_iso: int = 1
+    learn_pupil: int = 1
+    pupil_filter: int = 1
+    alpha: float = -1.0
+    beta: float = -1.0
+    gamma1: float = 0.9
+    gamma2: float = 0.999
+    s0_psi: float = 1.0
+    s0_pupil: float = 1e-2
+    eta_opt: float = 1e-8
+    eta_h: float = 1e-12
+    tau_fid: float = 1e-6
+    tau_h: float = 1e-4
+
+
+@dataclasses.dataclass
+class Geometry:
+    n: int                 # low-res side, B = n*n
+    u: int                 # upsampling, N = u*n
+    N: int                 # high-res side, A = N*N
+    dk: float              # spectral pixel (cycles/um), same on both grids
+    offsets: np.ndarray    # int64 [K, 2] = (c_y, c_x) in spectral pixels (A3)
+    origins: np.ndarray    # int64 [K, 2] = crop window top-left (row, col) in Psi
+    support: np.ndarray    # bool [n, n] pupil support S (A4)
+
+    @property
+    def K(self) -> int:
+        return int(self.offsets.shape[0])
+
+
+def round_half_away(x):
+    """Round to nearest, halves away from zero (A3)."""
+    x = np.asarray(x, dtype=np.float64)
+    return (np.sign(x) * np.floor(np.abs(x) + 0.5)).astype(np.int64)
+
+
+def make_geometry(n, u, k_xy, na, wavelength_um, pixel_um) -> Geometry:
+    """Crop windows M_n and pupil support of the forward model (Sec. 3.1, Eq. 1).
+
+    k_xy: [K, 2] illumination spatial frequency (kx, ky) in cycles/um.
+    pixel_um: low-res pixel size at the sample plane.
+    The spectral spacing is dk = 1/(n*pixel_um) on both grids (N*pixel_um/u = n*pixel_um).
+    """
+    n = int(n)
+    u = int(u)
+    N = n * u
+    dk = 1.0 / (n * float(pixel_um))
+    k_xy = np.asarray(k_xy, dtype=np.float64).reshape(-1, 2)
+    cy = round_half_away(k_xy[:, 1] / dk)
+    cx = round_half_away(k_xy[:, 0] / dk)
+    offsets = np.stack([cy, cx], axis=1)
+    origins = offsets + (N // 2 - n // 2)
+    if np.any(origins < 0) or np.any(origins + n > N):
+        raise ValueError("an LED crop window falls outside the high-res spectrum")
+    j = np.arange(n) - n // 2
+    rho2 = (j[None, :] ** 2 + j[:, None] ** 2) * dk * dk
+    support = rho2 <= (float(na) / float(wavelength_um)) ** 2
+    return Geometry(n=n, u=u, N=N, dk=dk, offsets=offsets, origins=origins, support=support)
+
+
+# ----------------------------------------------------------------------------
+# forward model (Sec. 3.1, Eq. 1 with M = 1)
+# ----------------------------------------------------------------------------
+def crop(psi, geo: Geometry, led: int):
+    """M_n Psi: the n x n window of the centred spectrum for LED ``led``."""
+    oy, ox = geo.origins[led]
+    return psi[oy:oy + geo.n, ox:ox + geo.n]
+
+
+def crop_adjoint(tile, geo: Geometry, led: int):
+    """M_n^T: put an n x n tile back at its place in an N x N zero spectrum."""
+    out = np.zeros((geo.N, geo.N), dtype=np.complex128)
+    oy, ox = geo.origins[led]
+    out[oy:oy + geo.n, ox:ox + geo.n] = tile
+    return out
+
+
+def forward_field(psi, pupil, geo: Geometry, led: int):
+    """o_n = F_B P M_n Psi (Eq. 1, A1): u^-2 * IDFT_n(ifftshift(P o crop))."""
+    p = pupil * geo.support
+    t = p * crop(psi, geo, led)
+    return np.fft.ifft2(np.fft.ifftshift(t)) / (geo.u * geo.u)
+
+
+def forward_intensity(psi, pupil, geo: Geometry):
+    """Predicted low-res intensities |o_n|^2 for every LED, float64 [K, n, n]."""
+    out = np.empty((geo.K, geo.n, geo.n), dtype=np.float64)
+    for k in range(geo.K):
+        out[k] = np.abs(forward_field(psi, pupil, geo, k)) ** 2
+    return out
+
+
+# ----------------------------------------------------------------------------
+# first-order difference operator (A5) and its adjoint
+# ----------------------------------------------------------------------------
+def grad_op(r):
+    """nabla r = (nabla_x r, nabla_y r): forward differences, zero on the last column/row."""
+    gx = np.zeros_like(r)
+    gy = np.zeros_like(r)
+    gx[:, :-1] = r[:, 1:] - r[:, :-1]
+    gy[:-1, :] = r[1:, :] - r[:-1, :]
+    return gx, gy
+
+
+def grad_adj(px, py):
+    """nabla^T (px, py): the exact transpose of grad_op."""
+    out = np.zeros_like(px)
+    out[:, 1:] += px[:, :-1]
+    out[:, :-1] -= px[:, :-1]
+    out[1:, :] += py[:-1, :]
+    out[:-1, :] -= py[:-1, :]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the normaliser omega of Eq. 12 under the smoothing reading A7
+# ----------------------------------------------------------------------------
+def huber(comps, tau, iso):
+    """Per-pixel cost phi_tau and its gradient omega (Eq. 12 with A7).
+
+    comps: list of equally shaped arrays (the components of the feature vector).
+    iso=1: phi = ||x||_2 if ||x|| >= tau else ||x||^2/(2 tau) + tau/2,
+           omega = x / max(||x||, tau).
+    iso=0: the same rule on each component separately (omega_i = x_i/max(|x_i|,tau)).
+    Returns (cost array, list of omega arrays).
+    """
+    if iso:
+        norm = np.sqrt(sum(c * c for c in comps))
+        cost = np.where(norm >= tau, norm, norm * norm / (2.0 * tau) + tau / 2.0)
+        den = np.maximum(norm, tau)
+        return cost, [c / den for c in comps]
+    cost = np.zeros_like(comps[0])
+    omegas = []
+    for c in comps:
+        a = np.abs(c)
+        cost = cost + np.where(a >= tau, a, a * a / (2.0 * tau) + tau / 2.0)
+        omegas.append(c / np.maximum(a, tau))
+    return cost, omegas
+
+
+# ----------------------------------------------------------------------------
+# second-order operator H (A6) and its adjoint
+# ----------------------------------------------------------------------------
+def hessian_op(f):
+    """H f = (Dxx, Dyy, sqrt(2) Dxy) on the interior (1..N-2)^2, zero elsewhere (Sec. 3.2)."""
+    dxx = np.zeros_like(f)
+    dyy = np.zeros_like(f)
+    dxy = np.zeros_like(f)
+    c = f[1:-1, 1:-1]
+    dxx[1:-1, 1:-1] = f[1:-1, :-2] - 2.0 * c + f[1:-1, 2:]
+    dyy[1:-1, 1:-1] = f[:-2, 1:-1] - 2.0 * c + f[2:, 1:-1]
+    dxy[1:-1, 1:-1] = (f[2:, 2:] - f[2:, :-2] - f[:-2, 2:] + f[:-2, :-2]) / 4.0
+    return dxx, dyy, math.sqrt(2.0) * dxy
+
+
+def hessian_adj(wxx, wyy, wxy):
+    """H^T (wxx, wyy, wxy): exact transpose of hessian_op (inputs live on the interior)."""
+    out = np.zeros_like(wxx)
+    a = wxx[1:-1, 1:-1]
+    out[1:-1, :-2] += a
+    out[1:-1, 1:-1] -= 2.0 * a
+    out[1:-1, 2:] += a
+    b = wyy[1:-1, 1:-1]
+    out[:-2, 1:-1] += b
+    out[1:-1, 1:-1] -= 2.0 * b
+    out[2:, 1:-1] += b
+    c = math.sqrt(2.0) * wxy[1:-1, 1:-1] / 4.0
+    out[2:, 2:] += c
+    out[2:, :-2] -= c
+    out[:-2, 2:] -= c
+    out[:-2, :-2] += c
+    return out
+
+
+# ----------------------------------------------------------------------------
+# data fidelity (Eqs. 4-5) and its Wirtinger gradients (Eqs. 9-11, 18)
+# ----------------------------------------------------------------------------
+def fidelity_cost_grad(psi, pupil, I, geo: Geometry, opt: Options, want_tiles=False):
+    """L_fid and its gradients with respect to conj(Psi) and conj(P).
+
+    For each LED (Algorithm 1, inner loops):
+      o_n = forward_field                                  (Eq. 1)
+      r_n = |o_n|^2 - I_n            (intensity, Eq. 5, A8)
+          = |o_n| - sqrt(max(I_n,0)) (amplitude, Eq. 4)
+      d = nabla r_n; (phi, omega) = huber(d)               (Eq. 12, A7)
+      W_n = o_n o nabla^T omega            (intensity, Eq. 11)
+          = o_n / (2 max(|o_n|, eta_H)) o nabla^T omega     (amplitude, Eq. 10, A11)
+      G_n = u^-2 n^-2 fftshift(DFT_n(W_n))                 (F_B^H of Eq. 9)
+    then (sums in ascending LED order)
+      g_Psi = sum_n M_n^T (conj(P) o G_n)                  (Eq. 9)
+      g_P   = sum_n conj(M_n Psi) o G_n, masked to S       (Eq. 18)
+    Returns (L_fid, g_psi [N,N], g_pupil [n,n], tiles [K,n,n] or None).
+    """
+    n, u = geo.n, geo.u
+    mask = geo.support
+    p_eff = pupil * mask
+    g_psi = np.zeros((geo.N, geo.N), dtype=np.complex128)
+    g_p = np.zeros((n, n), dtype=np.complex128)
+    tiles = np.zeros((geo.K, n, n), dtype=np.complex128) if want_tiles else None
+    cost = 0.0
+    for k in range(geo.K):
+        o = forward_field(psi, pupil, geo, k)
+        amp = np.abs(o)
+        if opt.fidelity == 0:
+            r = amp * amp - I[k]
+        else:
+            r = amp - np.sqrt(np.maximum(I[k], 0.0))
+        dx, dy = grad_op(r)
+        phi, (wx, wy) = huber([dx, dy], opt.tau_fid, opt.omega_iso)
+        cost += float(np.sum(phi))
+        w = grad_adj(wx, wy)
+        if opt.fidelity == 0:
+            W = o * w
+        else:
+            W = o / (2.0 * np.maximum(amp, opt.eta_h)) * w
+        G = np.fft.fftshift(np.fft.fft2(W)) / (u * u * n * n)
+        if want_tiles:
+            tiles[k] = G
+        g_psi += crop_adjoint(np.conj(p_eff) * G, geo, k)
+        g_p += np.conj(crop(psi, geo, k)) * G
+    g_p = g_p * mask
+    return cost, g_psi, g_p, tiles
+
+
+# ----------------------------------------------------------------------------
+# Hessian regulariser (Eqs. 6-7) and its gradients (Eqs. 13-14)
+# ----------------------------------------------------------------------------
+def object_from_spectrum(psi):
+    """O = IDFT_N(ifftshift(Psi)) (A1; Algorithm 1's O <- F_A^-1 Psi)."""
+    return np.fft.ifft2(np.fft.ifftshift(psi))
+
+
+def spectrum_from_object(obj):
+    """Psi = fftshift(DFT_N(O)) (A1; Sec. 3.1)."""
+    return np.fft.fftshift(np.fft.fft2(obj))
+
+
+def hessian_cost_grad(psi, alpha, beta, opt: Options):
+    """alpha L_A + beta L_Phi and its gradient with respect to conj(Psi).
+
+      O = object_from_spectrum(Psi);  a = |O|;  phi = atan2(Im O, Re O)   (A12)
+      (L_A, omega_a)   = huber(H a)                                     (Eq. 6)
+      (L_Phi, omega_p) = huber(H phi)                                   (Eq. 7)
+      q = alpha O/(2 max(a, eta_H)) H^T omega_a
+        + beta (i/2) O/(a^2 + eta_H) H^T omega_p                        (Eqs. 13-14, A13)
+      g_H = (1/A) fftshift(DFT_N(q))                                    (F_A^H)
+    Returns (L_A, L_Phi, g_H).  L_A and L_Phi are not weighted by alpha/beta.
+    """
+    N = psi.shape[0]
+    obj = object_from_spectrum(psi)
+    a = np.abs(obj)
+    ph = np.arctan2(obj.imag, obj.real)
+    interior = np.zeros((N, N), dtype=bool)
+    interior[1:-1, 1:-1] = True
+    ha = hessian_op(a)
+    cost_a, wa = huber(list(ha), opt.tau_h, opt.omega_iso)
+    hp = hessian_op(ph)
+    cost_p, wp = huber(list(hp), opt.tau_h, opt.omega_iso)
+    L_A = float(np.sum(cost_a[interior]))
+    L_P = float(np.sum(cost_p[interior]))
+    wa = [w * interior for w in wa]
+    wp = [w * interior for w in wp]
+    ta = hessian_adj(*wa)
+    tp = hessian_adj(*wp)
+    q = alpha * obj / (2.0 * np.maximum(a, opt.eta_h)) * ta
+    q = q + beta * 0.5j * obj / (a * a + opt.eta_h) * tp
+    g = np.fft.fftshift(np.fft.fft2(q)) / (N * N)
+    return L_A, L_P, g
+
+
+# ----------------------------------------------------------------------------
+# modified AdaBelief (Eq. 19)
+# ----------------------------------------------------------------------------
+def adabelief(x, g, mu, v, delta, t, opt: Options):
+    """One step of Eq. 19 at iteration index t >= 1 (g is dL/d(conj x), A11).
+
+      mu    = g1 mu + (1 - g1) g
+      v     = g2 v + (1 - g2) |mu - g|^2
+      mu^   = mu / (1 - g1^t);  v^ = v / (1 - g2^t)
+      Delta = (sqrt(delta) + eta)/(sqrt(v^) + eta) * (g1 mu^ + (1 - g1) g)
+      x     = x - Delta
+      delta = g1 delta + (1 - g1) |Delta|^2
+    Returns (x, mu, v, delta, Delta).
+    """
+    g1, g2, eta = opt.gamma1, opt.gamma2, opt.eta_opt
+    mu = g1 * mu + (1.0 - g1) * g
+    v = g2 * v + (1.0 - g2) * np.abs(mu - g) ** 2
+    mu_hat = mu / (1.0 - g1 ** t)
+    v_hat = v / (1.0 - g2 ** t)
+    step = (np.sqrt(delta) + eta) / (np.sqrt(v_hat) + eta) * (g1 * mu_hat + (1.0 - g1) * g)
+    x = x - step
+    delta = g1 * delta + (1.0 - g1) * np.abs(step) ** 2
+    return x, mu, v, delta, step
+
+
+# ----------------------------------------------------------------------------
+# pupil smoothing (note under Algorithm 1)
+# ----------------------------------------------------------------------------
+def gauss3():
+    """3 x 3 Gaussian kernel of width (sigma) 1 pixel, normalised to sum 1."""
+    g = np.exp(-0.5 * np.arange(-1, 2, dtype=np.float64) ** 2)
+    k = np.outer(g, g)
+    return k / k.sum()
+
+
+def filter3(p):
+    """G3 (x) P with zero padding outside the n x n grid."""
+    k = gauss3()
+    n0, n1 = p.shape
+    pad = np.zeros((n0 + 2, n1 + 2), dtype=p.dtype)
+    pad[1:-1, 1:-1] = p
+    out = np.zeros_like(p)
+    for dy in range(3):
+        for dx in range(3):
+            out += k[dy, dx] * pad[dy:dy + n0, dx:dx + n1]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# automatic regularisation weight (Eqs. 16-17, A10)
+# ----------------------------------------------------------------------------
+LAPLACE_KERNEL = np.array([[-1.0, 2.0, -1.0], [-2.0, 4.0, -2.0], [-1.0, 2.0, -1.0]])
+
+
+def alpha_estimate(I, amplitude=False):
+    """alpha = beta = (1/5) sqrt(pi/2) * mean_n mean_interior |I_n (x) L| (Eq. 16),
+    or of sqrt(I_n) for the amplitude fidelity (Eq. 17).  'valid' 3x3 window."""
+    I = np.asarray(I, dtype=np.float64)
+    if amplitude:
+        I = np.sqrt(np.maximum(I, 0.0))
+    K, h, w = I.shape
+    acc = np.zeros((K, h - 2, w - 2))
+    for dy in range(3):
+        for dx in range(3):
+            acc += LAPLACE_KERNEL[dy, dx] * I[:, dy:dy + h - 2, dx:dx + w - 2]
+    return 0.2 * math.sqrt(math.pi / 2.0) * float(np.mean(np.abs(acc)))
+
+
+# ----------------------------------------------------------------------------
+# state, initialisation (A9) and the iteration (Algorithm 1)
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class State:
+    psi: np.ndarray
+    mu_psi: np.ndarray
+    v_psi: np.ndarray
+    delta_psi: np.ndarray
+    pupil: np.ndarray
+    mu_p: np.ndarray
+    v_p: np.ndarray
+    delta_p: np.ndarray
+    t: int
+    alpha: float
+    beta: float
+
+    def copy(self) -> "State":
+        return State(**{f.name: (getattr(self, f.name).copy()
+                                 if isinstance(getattr(self, f.name), np.ndarray)
+                                 else getattr(self, f.name))
+                        for f in dataclasses.fields(self)})
+
+
+def centre_led(k_xy):
+    """Index of the LED closest to the optical axis (lowest index on ties)."""
+    k = np.asarray(k_xy, dtype=np.float64).reshape(-1, 2)
+    return int(np.argmin(k[:, 0] ** 2 + k[:, 1] ** 2))
+
+
+def init_state(I, geo: Geometry, k_xy, opt: Options) -> State:
+    """Initial state (A9): Psi0 from the centre-LED image, P0 = 1 on S.
+
+    Psi0 = u^2 * (fftshift(DFT_n(sqrt(max(I_c, 0)))) with its Nyquist row and
+    column zeroed), placed at the centre LED's crop window; mu = v = 0;
+    delta = s0^2; alpha, beta from Eq. 16/17 when negative in the options.
+    """
+    n, u, N = geo.n, geo.u, geo.N
+    c = centre_led(k_xy)
+    small = np.fft.fftshift(np.fft.fft2(np.sqrt(np.maximum(I[c], 0.0)))) * (u * u)
+    small[0, :] = 0.0
+    small[:, 0] = 0.0
+    psi = crop_adjoint(small, geo, c)
+    pupil = geo.support.astype(np.complex128)
+    a_auto = None
+    if opt.alpha < 0 or opt.beta < 0:
+        a_auto = alpha_estimate(I, amplitude=(opt.fidelity == 1))
+    alpha = a_auto if opt.alpha < 0 else float(opt.alpha)
+    beta = a_auto if opt.beta < 0 else float(opt.beta)
+    return State(
+        psi=psi,
+        mu_psi=np.zeros((N, N), dtype=np.complex128),
+        v_psi=np.zeros((N, N)),
+        delta_psi=np.full((N, N), opt.s0_psi ** 2),
+        pupil=pupil,
+        mu_p=np.zeros((n, n), dtype=np.complex128),
+        v_p=np.zeros((n, n)),
+        delta_p=np.full((n, n), opt.s0_pupil ** 2),
+        t=0, alpha=float(alpha), beta=float(beta))
+
+
+def iteration(state: State, I, geo: Geometry, opt: Options, want=False):
+    """One outer iteration of Algorithm 1 from state t to t+1.
+
+    Gradients are evaluated at (Psi^t, P^t) (Sec. 3.3-3.4), then Psi and P are
+    updated with Eq. 19; P is Gaussian-filtered before its update (A15).
+    Returns (new_state, costs=(L_fid, L_A, L_Phi) at state t, extras or None).
+    """
+    L_fid, g_fid, g_p, tiles = fidelity_cost_grad(state.psi, state.pupil, I, geo, opt,
+                                                  want_tiles=want)
+    L_A, L_P, g_h = hessian_cost_grad(state.psi, state.alpha, state.beta, opt)
+    g_psi = g_fid + g_h
+    t = state.t + 1
+    s = state.copy()
+    s.t = t
+    s.psi, s.mu_psi, s.v_psi, s.delta_psi, _ = adabelief(
+        state.psi, g_psi, state.mu_psi, state.v_psi, state.delta_psi, t, opt)
+    if opt.learn_pupil:
+        p_base = filter3(state.pupil) if opt.pupil_filter else state.pupil
+        p_new, s.mu_p, s.v_p, s.delta_p, _ = adabelief(
+            p_base, g_p, state.mu_p, state.v_p, state.delta_p, t, opt)
+        s.pupil = p_new * geo.support
+    extras = None
+    if want:
+        extras = dict(g_fid=g_fid, g_h=g_h, g_p=g_p, tiles=tiles)
+    return s, (L_fid, L_A, L_P), extras
+
+
+def run(state: State, I, geo: Geometry, opt: Options, n_iter: int):
+    """n_iter iterations; returns (final state, costs [n_iter, 3])."""
+    costs = []
+    for _ in range(n_iter):
+        state, c, _ = iteration(state, I, geo, opt)
+        costs.append(c)
+    return state, np.asarray(costs, dtype=np.float64).reshape(-1, 3)
+
+
+def total_cost(costs, alpha, beta):
+    """Eq. 8: L = L_fid + alpha L_A + beta L_Phi."""
+    c = np.asarray(costs, dtype=np.float64)
+    return c[..., 0] + alpha * c[..., 1] + beta * c[..., 2]

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the DFT
+definition summed by brute force, Parseval, exact adjoint identities, central
+finite differences, the affine null space of the Hessian, closed forms for
+Eq. 16 and for Eq. 19, a zero gradient at the true state, noiseless convergence,
+and the constants the paper prints (tests/golden/paper_constants.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+# --------------------------------------------------------------------------- helpers
+def tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0):
+    """Geometry with exact integer LED offsets (k = c * dk) and a pupil of radius na_px."""
+    dk = 1.0 / n  # pixel 1 um
+    c = (np.arange(grid) - (grid - 1) // 2) * step
+    cy, cx = np.meshgrid(c, c, indexing="ij")
+    k_xy = np.stack([cx.ravel() * dk, cy.ravel() * dk], axis=1)
+    geo = O.make_geometry(n, u, k_xy, na=na_px * dk, wavelength_um=1.0, pixel_um=1.0)
+    return geo, k_xy
+
+
+def smooth_object(N, seed, amp=(0.3, 1.0), ph=(-1.0, 1.0), sigma=4.0):
+    g = np.random.default_rng(seed)
+    f = np.fft.fftfreq(N) * N
+    filt = np.exp(-(f[None, :] ** 2 + f[:, None] ** 2) / (2 * sigma ** 2))
+
+    def field():
+        x = np.real(np.fft.ifft2(np.fft.fft2(g.standard_normal((N, N))) * filt))
+        return (x - x.min()) / (x.max() - x.min())
+    a = amp[0] + (amp[1] - amp[0]) * field()
+    p = ph[0] + (ph[1] - ph[0]) * field()
+    return a * np.exp(1j * p)
+
+
+def centred(k, n):
+    """centred spectral index -> frequency (index - n/2)."""
+    return k - n // 2
+
+
+# --------------------------------------------------------------------------- constants
+def test_constants_match_paper():
+    gold = json.load(open(GOLDEN))
+    assert np.array_equal(O.LAPLACE_KERNEL, np.array(gold["laplace_kernel"]["value"], float))
+    opt = O.Options()
+    assert opt.gamma1 == gold["gamma1_default"]["value"]
+    assert opt.gamma2 == gold["gamma2_default"]["value"]
+    assert opt.s0_psi ** 2 == gold["delta0"]["value"]
+    k = O.gauss3()
+    assert k.shape == (gold["pupil_filter"]["size"],) * 2
+    # sigma = 1 px: the ratio of an edge weight to the centre weight is exp(-1/2)
+    assert math.isclose(k[1, 0] / k[1, 1], math.exp(-0.5 / gold["pupil_filter"]["sigma_px"] ** 2))
+    assert math.isclose(k.sum(), 1.0)
+
+
+def test_round_half_away_and_support():
+    assert list(O.round_half_away([2.5, -2.5, 0.49, -0.51, 1.5])) == [3, -3, 0, -1, 2]
+    geo, _ = tiny_problem(n=16, na_px=5.0)
+    # explicit count of integer points with jx^2 + jy^2 <= 25
+    cnt = sum(1 for a in range(-8, 8) for b in range(-8, 8) if a * a + b * b <= 25)
+    assert geo.support.sum() == cnt == 81
+    assert geo.support[8, 8] and geo.support[8, 13] and not geo.support[8, 14]
+
+
+def test_geometry_offsets_round_half_away():
+    dk = 1.0 / 16
+    geo = O.make_geometry(16, 2, [[2.5 * dk, -2.5 * dk], [-0.5 * dk, 1.5 * dk]], na=0.2,
+                          wavelength_um=1.0, pixel_um=1.0)
+    assert geo.offsets.tolist() == [[-3, 3], [2, -1]]
+    assert geo.origins.tolist() == [[16 - 8 - 3, 16 - 8 + 3], [16 - 8 + 2, 16 - 8 - 1]]
+
+
+def test_geometry_rejects_out_of_range_window():
+    with pytest.raises(ValueError):
+        O.make_geometry(16, 2, [[20 / 16.0, 0.0]], na=0.2, wavelength_um=1.0, pixel_um=1.0)
+
+
+# --------------------------------------------------------------------------- transforms (A1)
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_object_from_spectrum_is_the_centred_idft(N):
+    g = np.random.default_rng(N)
+    psi = g.standard_normal((N, N)) + 1j * g.standard_normal((N, N))
+    # definition: O[y,x] = (1/A) sum_k Psi[k] exp(2 pi i (k - N/2).x / N)
+    want = np.zeros((N, N), complex)
+    for y in range(N):
+        for x in range(N):
+            for ky in range(N):
+                for kx in range(N):
+                    want[y, x] += psi[ky, kx] * np.exp(
+                        2j * np.pi * (centred(ky, N) * y + centred(kx, N) * x) / N)
+    want /= N * N
+    assert np.allclose(O.object_from_spectrum(psi), want, atol=1e-13)
+    assert np.allclose(O.spectrum_from_object(O.object_from_spectrum(psi)), psi, atol=1e-12)
+
+
+def test_forward_field_brute_force():
+    geo, _ = tiny_problem(n=8, u=2, grid=1, na_px=3.0)
+    g = np.random.default_rng(1)
+    psi = g.standard_normal((16, 16)) + 1j * g.standard_normal((16, 16))
+    pupil = g.standard_normal((8, 8)) + 1j * g.standard_normal((8, 8))
+    t = (pupil * geo.support) * psi[4:12, 4:12]
+    # o[y,x] = u^-2 (1/B) sum_j t[j] exp(2 pi i (j - n/2).x / n)
+    want = np.zeros((8, 8), complex)
+    for y in range(8):
+        for x in range(8):
+            for jy in range(8):
+                for jx in range(8):
+                    want[y, x] += t[jy, jx] * np.exp(2j * np.pi * ((jy - 4) * y + (jx - 4) * x) / 8)
+    want /= 64 * 4
+    assert np.allclose(O.forward_field(psi, pupil, geo, 0), want, atol=1e-13)
+
+
+def test_plane_wave_and_uniform_object():
+    N = 16
+    psi = np.zeros((N, N), complex)
+    psi[N // 2 + 3, N // 2 - 2] = 1.0
+    obj = O.object_from_spectrum(psi)
+    yy, xx = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    assert np.allclose(obj, np.exp(2j * np.pi * (3 * yy - 2 * xx) / N) / (N * N), atol=1e-15)
+    # uniform object through the on-axis LED with P(0)=1 images to itself (u^-2 scaling)
+    geo, _ = tiny_problem(n=8, u=2, grid=1, na_px=2.0)
+    obj = np.full((16, 16), 0.7 - 0.2j)
+    o = O.forward_field(O.spectrum_from_object(obj), np.ones((8, 8)), geo, 0)
+    assert np.allclose(o, 0.7 - 0.2j, atol=1e-13)
+
+
+def test_parseval():
+    g = np.random.default_rng(3)
+    obj = g.standard_normal((32, 32)) + 1j * g.standard_normal((32, 32))
+    psi = O.spectrum_from_object(obj)
+    assert math.isclose(np.sum(np.abs(psi) ** 2), 32 * 32 * np.sum(np.abs(obj) ** 2), rel_tol=1e-12)
+
+
+# --------------------------------------------------------------------------- adjoints
+def _inner(a, b):
+    return np.vdot(a, b)
+
+
+def test_adjoint_identities():
+    g = np.random.default_rng(5)
+    r = g.standard_normal((12, 9))
+    px, py = g.standard_normal((12, 9)), g.standard_normal((12, 9))
+    gx, gy = O.grad_op(r)
+    assert math.isclose(np.sum(gx * px) + np.sum(gy * py), np.sum(r * O.grad_adj(px, py)), rel_tol=1e-12)
+    f = g.standard_normal((11, 13))
+    w = [g.standard_normal((11, 13)) for _ in range(3)]
+    for c in w:  # H^T is applied to fields living on the interior
+        c[0, :] = c[-1, :] = 0
+        c[:, 0] = c[:, -1] = 0
+    h = O.hessian_op(f)
+    lhs = sum(np.sum(a * b) for a, b in zip(h, w))
+    assert math.isclose(lhs, np.sum(f * O.hessian_adj(*w)), rel_tol=1e-12)
+    p = g.standard_normal((10, 10)) + 1j * g.standard_normal((10, 10))
+    q = g.standard_normal((10, 10)) + 1j * g.standard_normal((10, 10))
+    assert abs(_inner(O.filter3(p), q) - _inner(p, O.filter3(q))) < 1e-12
+    geo, _ = tiny_problem(n=8, u=2, grid=3, step=2, na_px=3.0)
+    big = g.standard_normal((16, 16)) + 1j * g.standard_normal((16, 16))
+    small = g.standard_normal((8, 8)) + 1j * g.standard_normal((8, 8))
+    for k in range(geo.K):
+        assert abs(_inner(O.crop(big, geo, k), small) - _inner(big, O.crop_adjoint(small, geo, k))) < 1e-12
+
+
+def test_fidelity_gradient_is_adjoint_of_forward_operator():
+    """With tau huge, phi = |d|^2/(2 tau) + tau/2 is quadratic, so the gradient of the
+    intensity fidelity must equal the explicit chain of adjoints built term by term."""
+    geo, _ = tiny_problem(n=8, u=2, grid=3, step=2, na_px=3.0)
+    opt = O.Options(tau_fid=1e6)
+    obj = smooth_object(16, 2)
+    psi = O.spectrum_from_object(obj)
+    pupil = np.exp(0.3j) * np.ones((8, 8))
+    I = np.random.default_rng(4).uniform(0, 1, (geo.K, 8, 8))
+    _, g_psi, g_p, _ = O.fidelity_cost_grad(psi, pupil, I, geo, opt)
+    # explicit T_n and T_n^H as dense matrices on the 8x8 tile (independent of fft helpers)
+    n = 8
+    j = np.arange(n) - n // 2
+    E = np.exp(2j * np.pi * np.outer(np.arange(n), j) / n) / n    # x <- centred j, 1D
+    want = np.zeros_like(psi)
+    for k in range(geo.K):
+        t = (pupil * geo.support) * O.crop(psi, geo, k)
+        o = E @ t @ E.T / 4.0
+        r = np.abs(o) ** 2 - I[k]
+        dx, dy = O.grad_op(r)
+        w = O.grad_adj(dx / 1e6, dy / 1e6)
+        W = o * w
+        G = E.conj().T @ W @ E.conj() / 4.0
+        want += O.crop_adjoint(np.conj(pupil * geo.support) * G, geo, k)
+    assert np.allclose(g_psi, want, atol=1e-12 * np.abs(want).max())
+
+
+# --------------------------------------------------------------------------- finite differences
+def _total(psi, pupil, I, geo, opt, alpha, beta):
+    L_fid, _, _, _ = O.fidelity_cost_grad(psi, pupil, I, geo, opt)
+    L_A, L_P, _ = O.hessian_cost_grad(psi, alpha, beta, opt)
+    return L_fid + alpha * L_A + beta * L_P
+
+
+@pytest.mark.parametrize("fidelity,iso", [(0, 1), (1, 1), (0, 0)])
+def test_gradient_matches_central_differences(fidelity, iso):
+    geo, k_xy = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)
+    opt = O.Options(fidelity=fidelity, omega_iso=iso, tau_fid=1e-3, tau_h=1e-3)
+    truth = smooth_object(geo.N, 11)
+    I = O.forward_intensity(O.spectrum_from_object(truth), np.ones((16, 16)), geo)
+    I = I + 0.01 * np.random.default_rng(12).standard_normal(I.shape)
+    psi = O.spectrum_from_object(smooth_object(geo.N, 13))
+    pupil = geo.support * np.exp(0.2j * np.random.default_rng(14).standard_normal((16, 16)))
+    alpha, beta = 0.05, 0.03
+    _, g_fid, g_p, _ = O.fidelity_cost_grad(psi, pupil, I, geo, opt)
+    _, _, g_h = O.hessian_cost_grad(psi, alpha, beta, opt)
+    g = g_fid + g_h
+    rng = np.random.default_rng(15)
+    for trial in range(4):
+        d = rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape)
+        d *= np.linalg.norm(psi) / np.linalg.norm(d)
+        h = 1e-7
+        fd = (_total(psi + h * d, pupil, I, geo, opt, alpha, beta)
+              - _total(psi - h * d, pupil, I, geo, opt, alpha, beta)) / (2 * h)
+        an = 2.0 * np.real(np.vdot(g, d))
+        assert abs(fd - an) <= 2e-5 * abs(an) + 1e-9, (trial, fd, an)
+        dp = (rng.standard_normal(pupil.shape) + 1j * rng.standard_normal(pupil.shape)) * geo.support
+        hp = 1e-7
+        fdp = (_total(psi, pupil + hp * dp, I, geo, opt, alpha, beta)
+               - _total(psi, pupil - hp * dp, I, geo, opt, alpha, beta)) / (2 * hp)
+        anp = 2.0 * np.real(np.vdot(g_p, dp))
+        assert abs(fdp - anp) <= 2e-5 * abs(anp) + 1e-9, (trial, fdp, anp)
+
+
+def test_zero_gradient_at_the_true_state():
+    """Noiseless data generated by the same model: r = 0, omega = 0, so W = 0."""
+    geo, _ = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)
+    opt = O.Options()
+    truth = O.spectrum_from_object(smooth_object(geo.N, 21))
+    pupil = geo.support.astype(complex)
+    I = O.forward_intensity(truth, pupil, geo)
+    L, g_psi, g_p, _ = O.fidelity_cost_grad(truth, pupil, I, geo, opt)
+    assert math.isclose(L, geo.K * 16 * 16 * opt.tau_fid / 2, rel_tol=1e-6)
+    assert np.abs(g_psi).max() < 1e-9 * np.abs(truth).max()
+    assert np.abs(g_p).max() < 1e-9
+
+
+# --------------------------------------------------------------------------- Hessian (A6)
+def test_hessian_null_space_and_cross_term():
+    N = 24
+    yy, xx = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    for f in (3.0 + 0.5 * xx - 0.25 * yy, np.ones((N, N))):
+        for c in O.hessian_op(f):
+            assert np.abs(c).max() < 1e-12
+    dxx, dyy, dxy = O.hessian_op(xx * yy)
+    assert np.allclose(dxy[1:-1, 1:-1], math.sqrt(2.0)) and np.abs(dxx).max() == 0 and np.abs(dyy).max() == 0
+    dxx, dyy, dxy = O.hessian_op(xx ** 2)
+    assert np.allclose(dxx[1:-1, 1:-1], 2.0) and np.abs(dyy).max() == 0 and np.abs(dxy).max() < 1e-12
+    # affine amplitude and affine phase (span inside (-pi, pi)): zero gradient, cost = tau/2 per pixel
+    amp = 0.5 + 0.01 * xx + 0.005 * yy
+    ph = -1.0 + 0.04 * xx + 0.03 * yy
+    psi = O.spectrum_from_object(amp * np.exp(1j * ph))
+    opt = O.Options()
+    L_A, L_P, g = O.hessian_cost_grad(psi, 1.0, 1.0, opt)
+    assert math.isclose(L_A, (N - 2) ** 2 * opt.tau_h / 2, rel_tol=1e-6)
+    assert math.isclose(L_P, (N - 2) ** 2 * opt.tau_h / 2, rel_tol=1e-6)
+    assert np.abs(g).max() < 1e-9
+
+
+def test_hessian_gradient_wrt_object_matches_differences():
+    """dL_A/d(conj O) and dL_Phi/d(conj O) (Eqs. 13-14 before F_A^H) by finite differences."""
+    N = 16
+    opt = O.Options(tau_h=1e-3)
+    obj = smooth_object(N, 31, sigma=2.0)
+    psi = O.spectrum_from_object(obj)
+    rng = np.random.default_rng(32)
+    for alpha, beta in ((1.0, 0.0), (0.0, 1.0)):
+        _, _, g = O.hessian_cost_grad(psi, alpha, beta, opt)
+
+        def L(p):
+            a, b, _ = O.hessian_cost_grad(p, alpha, beta, opt)
+            return alpha * a + beta * b
+        for _ in range(3):
+            d = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+            d *= np.linalg.norm(psi) / np.linalg.norm(d)
+            h = 1e-7
+            fd = (L(psi + h * d) - L(psi - h * d)) / (2 * h)
+            an = 2 * np.real(np.vdot(g, d))
+            assert abs(fd - an) <= 2e-5 * abs(an) + 1e-9
+
+
+# --------------------------------------------------------------------------- Eq. 16
+def test_alpha_closed_forms():
+    n = 20
+    assert O.alpha_estimate(np.full((3, n, n), 0.37)) == 0.0
+    yy, xx = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), indexing="ij")
+    I = np.stack([xx ** 2, xx ** 2])
+    # every interior response of [1 2 1]^T (x) [-1 2 -1] to x^2 is -(1+2+1)*2 = -8
+    want = 0.2 * math.sqrt(math.pi / 2) * 8.0
+    assert math.isclose(O.alpha_estimate(I), want, rel_tol=1e-12)
+    assert math.isclose(want, 2.0053026197048, rel_tol=1e-12)
+    # amplitude variant (Eq. 17) takes sqrt first: sqrt(x^4) = x^2
+    assert math.isclose(O.alpha_estimate(I ** 2, amplitude=True), want, rel_tol=1e-12)
+
+
+# --------------------------------------------------------------------------- Eq. 19
+def test_adabelief_first_step_closed_form():
+    opt = O.Options()
+    g = np.array([3 + 4j, -1e-3 + 2e-3j, 0.0])
+    x0 = np.array([1 + 1j, 2.0, -3j])
+    s0 = 0.7
+    x, mu, v, delta, step = O.adabelief(x0, g, np.zeros(3, complex), np.zeros(3), np.full(3, s0 ** 2), 1, opt)
+    # t = 1: mu^ = g, v^ = gamma1^2 |g|^2  =>  Delta = (s0 + eta)/(gamma1 |g| + eta) g
+    want = (s0 + opt.eta_opt) / (opt.gamma1 * np.abs(g) + opt.eta_opt) * g
+    assert np.allclose(step, want, rtol=1e-12, atol=0)
+    assert np.allclose(x, x0 - want)
+    assert step[2] == 0 and math.isclose(delta[2], opt.gamma1 * s0 ** 2)
+
+
+def test_adabelief_constant_gradient_closed_form():
+    """Constant g: mu_t = (1-g1^t) g so mu^ = g; v_t = (1-g2) g^2 sum_s g2^(t-s) g1^(2s)."""
+    opt = O.Options()
+    g1, g2 = opt.gamma1, opt.gamma2
+    g = np.array([0.3 - 0.4j])
+    x = np.zeros(1, complex)
+    mu = np.zeros(1, complex)
+    v = np.zeros(1)
+    delta = np.ones(1)
+    for t in range(1, 8):
+        x, mu, v, delta, _ = O.adabelief(x, g, mu, v, delta, t, opt)
+        assert np.allclose(mu, (1 - g1 ** t) * g, rtol=1e-13)
+        vt = (1 - g2) * abs(g[0]) ** 2 * sum(g2 ** (t - s) * g1 ** (2 * s) for s in range(1, t + 1))
+        assert math.isclose(v[0], vt, rel_tol=1e-12)
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+def test_initial_state_reproduces_centre_image():
+    """Psi0 built from the centre-LED image reproduces that image's amplitude (Nyquist aside)."""
+    geo, k_xy = tiny_problem(n=16, u=2, grid=3, step=4, na_px=8.0)
+    truth = O.spectrum_from_object(smooth_object(geo.N, 41, sigma=2.0))
+    I = O.forward_intensity(truth, geo.support.astype(complex), geo)
+    st = O.init_state(I, geo, k_xy, O.Options(alpha=0.0, beta=0.0))
+    assert O.centre_led(k_xy) == 4
+    o = O.forward_field(st.psi, np.ones((16, 16)), geo, 4)
+    assert np.abs(o.imag).max() < 1e-12
+    obj0 = O.object_from_spectrum(st.psi)        # Nyquist row/column zeroed => real O0
+    assert np.abs(obj0.imag).max() < 1e-12 * np.abs(obj0).max()
+    assert np.allclose(np.abs(o), np.sqrt(I[4]), atol=0.05)
+    assert st.t == 0 and np.all(st.delta_psi == 1.0) and np.all(st.delta_p == 1e-4)
+
+
+def test_noiseless_convergence():
+    """learn_pupil=0, alpha=beta=0, noiseless data: the fidelity drops by > 3 orders.
+    The rate is parity unpinned against the paper (which only says 'within 20 iterations')."""
+    geo, k_xy = tiny_problem(n=16, u=4, grid=5, step=3, na_px=4.5)
+    truth = O.spectrum_from_object(smooth_object(geo.N, 51, sigma=3.0))
+    I = O.forward_intensity(truth, geo.support.astype(complex), geo)
+    opt = O.Options(learn_pupil=0, alpha=0.0, beta=0.0, tau_fid=1e-9)
+    st = O.init_state(I, geo, k_xy, opt)
+    st, costs = O.run(st, I, geo, opt, 150)
+    floor = geo.K * 16 * 16 * opt.tau_fid / 2
+    assert (costs[-1, 0] - floor) < 1e-3 * (costs[0, 0] - floor), costs[[0, -1], 0]
+
+
+def test_hessian_fills_spectrum_beyond_passband():
+    """Sec. 4.2: with the Hessian term the recovered spectrum is nonzero beyond the
+    region the LEDs cover; the initial spectrum is zero there."""
+    geo, k_xy = tiny_problem(n=16, u=4, grid=3, step=3, na_px=4.0)
+    truth = O.spectrum_from_object(smooth_object(geo.N, 61, sigma=3.0))
+    I = O.forward_intensity(truth, geo.support.astype(complex), geo)
+    st = O.init_state(I, geo, k_xy, O.Options(alpha=0.05, beta=0.05))
+    corner = (slice(0, 8), slice(0, 8))
+    assert np.abs(st.psi[corner]).max() == 0
+    st2, _, _ = O.iteration(st, I, geo, O.Options(alpha=0.05, beta=0.05))
+    assert np.abs(st2.psi[corner]).min() > 0
