@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the Elfpie gradient step on GB300.
+
+One step = one outer iteration of Algorithm 1 over all K LEDs (every kernel of
+the iteration: tile kernel, Hessian branch, Eq. 9 gather + Eq. 19 update, Eq. 18
+pupil gradient and update, FP64 costs).  Metric: LED sub-image updates/s
+(K x iterations / s).  Default workload: 15x15 LEDs, 256x256 images, 1024x1024
+spectrum, mixed corruptions (seeded synthetic data).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload (the per-problem path does not shard); value = the units
+of all ranks / the max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2209_14671_gb300 import inputs as IN  # noqa: E402
+
+METRIC = "LED sub-image updates/s (K×iters/s) at fixed error vs FP64 oracle; p99 latency"
+UNIT = "LED sub-image updates/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "tile_kernel_traffic.json")
+TILE_SOURCES = ["paper_2209_14671_gb300/csrc/tile_kernel.cu", "paper_2209_14671_gb300/csrc/fft.cuh"]
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def tile_sources_hash() -> str:
+    h = hashlib.sha256()
+    for p in TILE_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    if os.path.exists(PEAKS_PATH):
+        d = json.load(open(PEAKS_PATH))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample_rate(I_host: np.ndarray, w: dict, seconds: float):
+    """FP64 oracle iterations of the same workload on the host cores, bounded to ~`seconds`."""
+    import oracle as O  # the CPU baseline legs are the only product-side users of the oracle
+    geo = O.make_geometry(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"])
+    opt = O.Options()
+    I = I_host.astype(np.float64)
+    st = O.init_state(I, geo, w["k_xy"], opt)
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        st, _, _ = O.iteration(st, I, geo, opt)
+        its += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or its >= 50:
+            break
+    return geo.K * its / el, its, el
+
+
+def make_inputs(w: dict, wid: int, torch, dev):
+    """Measurements of the workload: the GPU forward model (elf_simulate) at the true LED
+    positions, then the seeded degradations of the workload's recipe."""
+    from paper_2209_14671_gb300 import elfpie as E
+    obj = torch.from_numpy(IN.object_field(wid, w).astype(np.complex64)).to(dev)
+    with E.Elf(w["n"], w["u"], w["k_xy_true"], w["na"], w["wavelength_um"], w["pixel_um"]) as sim:
+        I_clean = torch.empty((w["K"], w["n"], w["n"]), dtype=torch.float32, device=dev)
+        sim.simulate(obj, I_clean)
+    return IN.corrupt(I_clean.cpu().numpy(), wid, w)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w = IN.problem(args.workload)
+    import oracle as O
+    geo_t = O.make_geometry(w["n"], w["u"], w["k_xy_true"], w["na"], w["wavelength_um"], w["pixel_um"])
+    obj = IN.object_field(args.workload, w)
+    I = IN.corrupt(O.forward_intensity(O.spectrum_from_object(obj), geo_t.support.astype(complex), geo_t),
+                   args.workload, w).astype(np.float64)
+    geo = O.make_geometry(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"])
+    opt = O.Options()
+    st = O.init_state(I, geo, w["k_xy"], opt)
+    # each step: one oracle iteration over a bounded LED sample (every 9th LED) + the full spectrum update
+    sample = np.arange(0, geo.K, 9)
+    geo_s = O.Geometry(n=geo.n, u=geo.u, N=geo.N, dk=geo.dk, offsets=geo.offsets[sample],
+                       origins=geo.origins[sample], support=geo.support)
+    I_s = I[sample]
+    for _ in range(args.warmup):
+        st, _, _ = O.iteration(st, I_s, geo_s, opt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _, _ = O.iteration(st, I_s, geo_s, opt)
+    el = time.perf_counter() - t0
+    val = len(sample) * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator, FP64 oracle forward model + workload degradations)",
+            "config": {"workload": w["name"], "n": w["n"], "N": w["N"], "K": w["K"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 oracle iteration per step over {len(sample)} of {geo.K} LEDs "
+                                       "(every 9th) plus the full spectrum-side update"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2209_14671_gb300 import build as B
+    from paper_2209_14671_gb300 import elfpie as E
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    B.build()
+    E.load()
+    wid = args.workload
+    w = IN.problem(wid)
+    I_host = make_inputs(w, wid, torch, dev)
+    I_dev = torch.from_numpy(I_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    elf = E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"], stream=stream)
+    elf.set_measurements(I_dev)
+    elf.set_tracing(True)
+    kernels_per_step = elf.kernels_per_step()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        elf.step(1)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = []
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()                     # L2 flush between timed iterations (outside the events)
+        starts[i].record(stream)
+        elf.step(1)
+        ends[i].record(stream)
+        stage_ms.append(elf.stage_times())  # synchronises after the step; tile kernel events from the graph
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    units = w["K"] * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # dominant kernel: the per-LED tile kernel
+    tile_ms = float(np.mean([s["tile"] for s in stage_ms]))
+    S = elf.S
+    tile_bytes = w["K"] * (4 * w["n"] ** 2 + 16 * S) + 8 * S
+    hbm, peak_kind = peaks()
+    achieved = tile_bytes / (tile_ms / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_PATH):
+        tr = json.load(open(TRAFFIC_PATH))
+        if tr.get("sources_sha256_16") == tile_sources_hash() and tr.get("workload") == w["name"]:
+            traffic = tr.get("dram_bytes_per_launch")
+    stage_mean = {k: float(np.mean([s[k] for s in stage_ms])) for k in stage_ms[0]}
+    it_bytes = w["K"] * (4 * w["n"] ** 2 + 32 * S) + 72 * w["N"] ** 2
+
+    # end to end through the public API with host buffers: one full reconstruction per step
+    e2e = None
+    if not args.no_e2e:
+        I_pin = torch.from_numpy(I_host).pin_memory()
+        O_pin = torch.empty((w["N"], w["N"]), dtype=torch.complex64).pin_memory()
+        elf.set_tracing(False)
+        jobs, warm = max(3, args.steps // 4), max(1, args.warmup // 2)
+        iters = w["iters"]
+        for _ in range(warm):
+            elf.set_measurements(I_pin.numpy())
+            elf.step(iters)
+            elf.get_object(O_pin.numpy())
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(jobs):
+            elf.set_measurements(I_pin.numpy())   # H2D of the job's measurements + initial state
+            elf.step(iters)
+            elf.get_object(O_pin.numpy())         # D2H of the reconstructed object (synchronises)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": w["K"] * iters * jobs * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(I_host.nbytes), "d2h_bytes_per_step": int(O_pin.numel() * 8),
+               "step": f"one reconstruction: elf_set_measurements(pinned host) + elf_step({iters}) + "
+                       f"elf_get_object(pinned host); {jobs} jobs timed by wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, its, el = oracle_sample_rate(I_host, w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{its} full FP64 oracle iterations of this workload ({w['K']} LEDs each), "
+                         f"{el:.1f} s on one host core (NumPy pocketfft, single-threaded)"}
+    elf.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded smooth random object, GPU forward model at jittered LED positions, "
+                    "workload degradations (Gaussian, Poisson, salt & pepper, background, vignetting)",
+            "config": {"workload": w["name"], "n": w["n"], "N": w["N"], "K": w["K"], "iters_per_step": 1,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
+                       "learn_pupil": 1, "fidelity": "intensity (Eq. 5)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "tile_kernel<256,8>",
+                         "algorithmic_bytes": tile_bytes, "launch_ms": tile_ms, "peak_source": peak_kind},
+            "iteration_roofline": {"algorithmic_bytes": it_bytes, "achieved_gbs": it_bytes / (total_ms / args.steps / 1e3) / 1e9,
+                                   "frac": it_bytes / (total_ms / args.steps / 1e3) / 1e9 / hbm},
+            "stage_ms": stage_mean,
+            "clocks": clk,
+            "gpu_launches": kernels_per_step * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * elfpie.h - C ABI of the GB300-native Elfpie gradient step.
+ *
+ * Elfpie (arXiv 2209.14671) reconstructs the high-resolution spectrum Psi of a
+ * sample and the pupil P of the objective from K low-resolution intensity
+ * images, one per LED, by minimising Eq. 8 (an L1 fidelity on spatial gradients,
+ * Eq. 5 or Eq. 4, plus a Hessian total-variation penalty on amplitude and phase,
+ * Eqs. 6-7) with the modified AdaBelief update of Eq. 19.  One call of
+ * elf_step(h, 1) is one outer iteration of Algorithm 1 over all K LEDs.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: ELF_OK (0) or a negative ELF_E* code; elf_last_error() gives
+ *    a message for the calling thread's last failure.
+ *  - Complex arrays are interleaved float pairs (re, im), row-major [y][x].
+ *    Spectra (Psi, pupil) are centred: zero frequency at index (N/2, N/2) of the
+ *    N x N spectrum and (n/2, n/2) of the n x n pupil.  Objects are spatial
+ *    fields with the usual (0, 0) origin.
+ *  - Buffers passed in are caller-owned; the library copies from them before the
+ *    call returns (or, for device buffers, in stream order) and keeps no pointer.
+ *    Buffers passed out are filled by the call.  "is_device" says whether a
+ *    pointer is device memory (1) or host memory (0); unified addressing makes
+ *    either work, the flag only documents intent.
+ *  - All device work of a handle is ordered on the CUDA stream given at
+ *    elf_create (0 = the legacy default stream).  elf_step returns without
+ *    synchronising; every elf_get_* call synchronises that stream.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - The LED order given at elf_create fixes every summation order, so results
+ *    are bitwise reproducible run to run on the same GPU.
+ *  - The library allocates its device memory in elf_create (cudaMalloc) and
+ *    frees it in elf_destroy.
+ */
+#ifndef ELFPIE_H
+#define ELFPIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ELF_OK = 0,
+  ELF_EINVAL = -1,    /* invalid argument or problem (crop outside the grid, unsupported size, K = 0, NaN input) */
+  ELF_ENOMEM = -2,    /* device allocation failed */
+  ELF_ECUDA = -3,     /* a CUDA runtime call failed; see elf_last_error() */
+  ELF_ENUMERIC = -4,  /* a non-finite cost was produced */
+  ELF_ETIMEOUT = -5,  /* a bounded wait ran out */
+  ELF_ESTATE = -6     /* call out of order (e.g. elf_step before elf_set_measurements) */
+};
+
+typedef struct elf_handle_s* elf_handle;
+
+/* Imaging geometry of Sec. 3.1 / Eq. 1 (sequential FPM, M = 1).
+ * The spectral pixel is dk = 1 / (n_lowres * pixel_um) cycles/um on both grids.
+ * LED n is placed at the centred offset c_n = round-half-away(k_n / dk) and its
+ * crop window is rows/cols [N/2 + c - n/2, N/2 + c + n/2), which must lie in
+ * [0, N).  The pupil support is {j : |j - n/2|^2 dk^2 <= (na / wavelength_um)^2}. */
+typedef struct {
+  int n_lowres;           /* n: low-res image side; 16, 32, 64, 128 or 256 */
+  int upsample;           /* u >= 1; N = u * n must be 32..1024 and a power of two */
+  int n_led;              /* K >= 1 */
+  const float* k_xy;      /* [K][2] (kx, ky) illumination spatial frequency, cycles/um; host, copied */
+  double na;              /* objective numerical aperture (> 0) */
+  double wavelength_um;   /* illumination wavelength (> 0) */
+  double pixel_um;        /* low-res pixel size at the sample plane (> 0) */
+} elf_problem;
+
+/* Hyper-parameters (Sec. 6.2) and the smoothing constants of the readings. */
+typedef struct {
+  int fidelity;      /* 0 = intensity (Eqs. 5, 11; default), 1 = amplitude (Eqs. 4, 10) */
+  int omega_iso;     /* 1 = isotropic normaliser of Eq. 12 (default), 0 = anisotropic */
+  int learn_pupil;   /* 1 = update P with Eq. 18 + Eq. 19 (default) */
+  int pupil_filter;  /* 1 = 3x3 Gaussian (sigma 1 px) on P before its update (note under Algorithm 1) */
+  double alpha;      /* Hessian amplitude weight of Eq. 8; < 0 = automatic (Eq. 16/17) */
+  double beta;       /* Hessian phase weight of Eq. 8; < 0 = automatic (Eq. 16/17) */
+  double gamma1;     /* Eq. 19 first-moment decay (0.9) */
+  double gamma2;     /* Eq. 19 belief decay (0.999) */
+  double s0_psi;     /* initial step of Psi: delta^0 = s0^2 (1) */
+  double s0_pupil;   /* initial step of P (1e-2) */
+  double eta_opt;    /* Eq. 19 eta (1e-8) */
+  double eta_h;      /* Eq. 14 eta and the |O| floor of Eq. 13 (1e-12) */
+  double tau_fid;    /* smoothing radius of the L1 fidelity (1e-6) */
+  double tau_h;      /* smoothing radius of the Hessian L1 terms (1e-4) */
+} elf_options;
+
+/* Full optimiser state of Eq. 19 for Psi and P (Algorithm 1 keeps nothing else).
+ * Every pointer is caller-owned.  Sizes: psi, mu_psi [N][N][2] float;
+ * v_psi, delta_psi [N][N] float; pupil, mu_pupil [n][n][2]; v_pupil, delta_pupil [n][n].
+ * t is the number of completed iterations. */
+typedef struct {
+  float* psi; float* mu_psi; float* v_psi; float* delta_psi;
+  float* pupil; float* mu_pupil; float* v_pupil; float* delta_pupil;
+  int t;
+  double alpha;
+  double beta;
+} elf_state;
+
+/* Fills *o with the defaults listed above. */
+int elf_default_options(elf_options* o);
+
+/* Validates the problem, precomputes LED offsets, the pupil support and the
+ * gather lists, and allocates all device memory (inputs, state, scratch).
+ * opt may be NULL (defaults).  cuda_stream is a cudaStream_t (may be NULL). */
+int elf_create(const elf_problem* prob, const elf_options* opt, void* cuda_stream, elf_handle* out);
+
+/* Copies the K measured images I [K][n][n] float (host or device) into the
+ * handle, estimates alpha = beta with Eq. 16 (Eq. 17 for the amplitude fidelity)
+ * when the options ask for it, and initialises the state (reading A9 of the
+ * design notes): Psi0 = u^2 * centred DFT of sqrt(max(I_c, 0)) of the LED nearest
+ * the axis, Nyquist row/column zeroed, placed at that LED's window; P0 = 1 on the
+ * support; mu = v = 0; delta = s0^2; t = 0.  Non-finite input -> ELF_EINVAL. */
+int elf_set_measurements(elf_handle h, const float* I, int is_device);
+
+/* Runs n_iter outer iterations of Algorithm 1 (Eqs. 9-19) asynchronously. */
+int elf_step(elf_handle h, int n_iter);
+
+/* Object O = IDFT_N(ifftshift(Psi)) (Algorithm 1 output), [N][N][2] float. */
+int elf_get_object(elf_handle h, float* obj, int is_device);
+/* Current pupil P, [n][n][2] float (zero outside the support). */
+int elf_get_pupil(elf_handle h, float* pupil, int is_device);
+/* Current centred spectrum Psi, [N][N][2] float. */
+int elf_get_spectrum(elf_handle h, float* psi, int is_device);
+/* Per-iteration FP64 costs (L_fid, L_A, L_Phi) of Eq. 8 evaluated at the state
+ * each iteration started from, oldest first, for the last min(t, max_iter, 4096)
+ * iterations, into out [count][3] (host).  Returns count (>= 0) or an error. */
+int elf_get_costs(elf_handle h, double* out, int max_iter);
+/* Copies the optimiser state out / in (checkpoint and resume). */
+int elf_get_state(elf_handle h, const elf_state* out, int is_device);
+int elf_set_state(elf_handle h, const elf_state* in, int is_device);
+
+/* Evaluates the cost of Eq. 8 and its Wirtinger gradients dL/d(conj Psi)
+ * (Eq. 15 = Eq. 9 + alpha Eq. 13 + beta Eq. 14) and dL/d(conj P) (Eq. 18) at the
+ * given (psi [N][N][2], pupil [n][n][2]) with the handle's measurements, alpha and
+ * beta, without touching the optimiser state.  costs3 (host) receives
+ * (L_fid, L_A, L_Phi) in FP64; g_psi / g_pupil (same layouts) may be NULL. */
+int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs3,
+                  float* g_psi, float* g_pupil, int is_device);
+
+/* Forward model of Eq. 1 for data synthesis: I_n = |o_n|^2 for every LED of the
+ * handle's geometry, from the spatial object obj [N][N][2] and the unit pupil on
+ * the support.  Writes I_out [K][n][n] float. */
+int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device);
+
+/* Inspection: the per-LED tile gradients G_n = u^-2 n^-2 fftshift(DFT_n(W_n))
+ * (the F_B^H W_n factor of Eq. 9) of the last elf_step / elf_cost_grad, stored on
+ * the pupil support only: G_out [K][S][2] float; the support pixels in that order
+ * are given by elf_get_support (linear indices jy*n + jx, ascending). */
+int elf_get_tile_grads(elf_handle h, float* G_out, int is_device);
+/* Number of support pixels S, and (if idx != NULL) their linear indices [S] (host). */
+int elf_get_support(elf_handle h, int* idx);
+/* alpha and beta in use (after elf_set_measurements). */
+int elf_get_weights(elf_handle h, double* alpha, double* beta);
+
+/* Tracing.  Stages of one iteration, timed with CUDA events recorded on the
+ * stream each stage runs on (inside the iteration graph when tracing is on). */
+enum {
+  ELF_STAGE_ITERATION = 0,     /* the whole iteration */
+  ELF_STAGE_TILE = 1,          /* per-LED tile kernel (Eqs. 1, 5, 11, 12, F_B^H of Eq. 9) */
+  ELF_STAGE_HESSIAN = 2,       /* O = F_A^-1 Psi, Eqs. 6-7, 13-14, F_A^H (second stream) */
+  ELF_STAGE_PUPIL_GRAD = 3,    /* Eq. 18 partial sums */
+  ELF_STAGE_GATHER = 4,        /* Eq. 9 gather fused with Eq. 19 for Psi */
+  ELF_STAGE_PUPIL_UPDATE = 5,  /* Gaussian filter + Eq. 19 for P */
+  ELF_STAGE_COST = 6,          /* FP64 reduction of Eq. 8's terms */
+  ELF_NSTAGES = 7
+};
+/* enable != 0 records the stage events from the next elf_step on (the graph is
+ * rebuilt); adds event nodes only, no extra kernels. */
+int elf_set_tracing(elf_handle h, int enable);
+/* Durations in ms of each stage of the most recent traced iteration, ms[ELF_NSTAGES]
+ * (-1 for a stage that did not run).  Synchronises.  Returns the count written. */
+int elf_get_stage_times(elf_handle h, float* ms, int max_stages);
+/* Number of kernel launches in one iteration (kernel nodes of the iteration graph). */
+int elf_graph_kernel_count(elf_handle h);
+
+void elf_destroy(elf_handle h);
+const char* elf_strerror(int code);
+const char* elf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELFPIE_H */

@@ -1,0 +1,787 @@
+// Host side of the C ABI declared in include/elfpie.h.
+//
+// elf_create validates the geometry of Sec. 3.1 (LED offsets, crop windows,
+// pupil support), builds the lookup tables the kernels use (support runs per
+// pupil row, compact support order, per-spectrum-tile LED lists for the
+// deterministic gather of Eq. 9) and allocates every device buffer once.
+// One iteration of Algorithm 1 is the launch sequence in enqueue_iteration; for
+// elf_step it is captured once into a CUDA graph whose Hessian branch
+// (Eqs. 6-7, 13-14) runs on a second stream concurrently with the tile kernel.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/elfpie.h"
+#include "internal.cuh"
+
+using namespace elf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define ELF_CK(call)                                                                               \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return set_error(e_ == cudaErrorMemoryAllocation ? ELF_ENOMEM : ELF_ECUDA,                   \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+double round_half_away(double x) { return (x < 0 ? -1.0 : 1.0) * std::floor(std::fabs(x) + 0.5); }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct elf_handle_s {
+  int n = 0, u = 0, N = 0, K = 0, S = 0, Blo = 0, nb = 0, rowsA = 0, cs = 1, Q = 1;
+  int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;
+  double dk = 0.0;
+  elf_options opt{};
+  cudaStream_t user = nullptr, cap = nullptr, aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool have_meas = false;
+  bool tracing = false;
+  int graph_kernels = 0;
+  cudaEvent_t ev_stage[2 * ELF_NSTAGES] = {};
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int2> origin_h;
+  std::vector<int> sidx_h;  // linear support indices in compact order
+  float gw0 = 0.f, gw1 = 0.f;
+  // device tables
+  int2* origin = nullptr;
+  int *row_xs = nullptr, *row_cnt = nullptr, *row_off = nullptr;
+  int *sup_y = nullptr, *sup_x = nullptr, *sidx_map = nullptr;
+  int *tile_ptr = nullptr, *tile_led = nullptr;
+  float2 *tw_n = nullptr, *tw_N = nullptr;
+  // data and state
+  float* I = nullptr;
+  float2 *psi = nullptr, *mu_psi = nullptr;
+  float *v_psi = nullptr, *delta_psi = nullptr;
+  float2 *pupil = nullptr, *pupil_next = nullptr, *mu_p = nullptr;
+  float *v_p = nullptr, *delta_p = nullptr;
+  // scratch
+  float2 *G = nullptr, *ot = nullptr, *q = nullptr, *small = nullptr, *part = nullptr;
+  float2 *psi_eval = nullptr, *pupil_eval = nullptr, *g_psi = nullptr, *g_p = nullptr, *pupil_unit = nullptr;
+  double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
+         *out3 = nullptr;
+  int *t_dev = nullptr, *flag = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(elf_handle h, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess)
+    return set_error(e == cudaErrorMemoryAllocation ? ELF_ENOMEM : ELF_ECUDA,
+                     std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return ELF_OK;
+}
+
+template <typename T>
+int upload(elf_handle h, T** p, const std::vector<T>& v) {
+  int rc = dalloc(h, p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) ELF_CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return ELF_OK;
+}
+
+std::vector<float2> twiddles(int L) {
+  std::vector<float2> t(L);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < L; ++k) {
+    const double a = -2.0 * pi * (double)k / (double)L;
+    t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+// Timing event of a stage boundary (recorded into the graph when tracing is on).
+int mark(elf_handle h, cudaStream_t s, int stage, int end) {
+  if (!h->tracing) return ELF_OK;
+  ELF_CK(cudaEventRecordWithFlags(h->ev_stage[2 * stage + end], s, cudaEventRecordExternal));
+  return ELF_OK;
+}
+
+#define ELF_MARK(s, stage, end)                          \
+  do {                                                   \
+    if (int rc_ = mark(h, (s), (stage), (end))) return rc_; \
+  } while (0)
+
+// One outer iteration of Algorithm 1 (mode 0) or a gradient evaluation (mode 1).
+int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil) {
+  const bool pupil_path = (mode == 1) || h->opt.learn_pupil;
+  const size_t A = (size_t)h->N * h->N;
+  ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
+  // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
+  ELF_CK(cudaEventRecord(h->ev_fork, s0));
+  ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+  ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
+  ELF_CK(cudaMemcpyAsync(h->ot, psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->aux));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux));
+  HessArgs ha{};
+  ha.ot = h->ot;
+  ha.q = h->q;
+  ha.costpart = h->cost_h;
+  ha.weights = h->weights;
+  ha.N = h->N;
+  ha.invA = (float)(1.0 / (double)A);
+  ha.tau = (float)h->opt.tau_h;
+  ha.eta = (float)h->opt.eta_h;
+  ha.iso = h->opt.omega_iso;
+  ELF_CK(launch_hessian(ha, h->aux));
+  ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux));
+  ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
+  ELF_CK(cudaEventRecord(h->ev_join, h->aux));
+
+  // tile path: Eqs. 1, 5 (4), 12, 11 (10) and F_B^H of Eq. 9
+  TileArgs ta{};
+  ta.psi = psi;
+  ta.pupil = pupil;
+  ta.meas = h->I;
+  ta.origin = h->origin;
+  ta.row_xs = h->row_xs;
+  ta.row_cnt = h->row_cnt;
+  ta.row_off = h->row_off;
+  ta.tw = h->tw_n;
+  ta.G = h->G;
+  ta.costpart = h->cost_fid;
+  ta.I_out = nullptr;
+  ta.N = h->N;
+  ta.K = h->K;
+  ta.S = h->S;
+  ta.Blo = h->Blo;
+  ta.nb = h->nb;
+  ta.rowsA = h->rowsA;
+  ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
+  ta.tau = (float)h->opt.tau_fid;
+  ta.eta = (float)h->opt.eta_h;
+  ta.fidelity = h->opt.fidelity;
+  ta.iso = h->opt.omega_iso;
+  ta.mode = 0;
+  ELF_MARK(s0, ELF_STAGE_TILE, 0);
+  ELF_CK(launch_tile(ta, h->n, s0));
+  ELF_MARK(s0, ELF_STAGE_TILE, 1);
+
+  PupilArgs pa{};
+  pa.G = h->G;
+  pa.psi = psi;
+  pa.origin = h->origin;
+  pa.sup_y = h->sup_y;
+  pa.sup_x = h->sup_x;
+  pa.sidx_map = h->sidx_map;
+  pa.part = h->part;
+  pa.pupil = pupil;
+  pa.pupil_next = h->pupil_next;
+  pa.mu = h->mu_p;
+  pa.v = h->v_p;
+  pa.delta = h->delta_p;
+  pa.g_out = h->g_p;
+  pa.t_dev = h->t_dev;
+  pa.N = h->N;
+  pa.n = h->n;
+  pa.S = h->S;
+  pa.K = h->K;
+  pa.Q = h->Q;
+  pa.filter = h->opt.pupil_filter;
+  pa.w0 = h->gw0;
+  pa.w1 = h->gw1;
+  pa.g1 = (float)h->opt.gamma1;
+  pa.g2 = (float)h->opt.gamma2;
+  pa.eta = (float)h->opt.eta_opt;
+  pa.mode = mode;
+  if (pupil_path) {
+    ELF_MARK(s0, ELF_STAGE_PUPIL_GRAD, 0);
+    ELF_CK(launch_pupil_partial(pa, s0));
+    ELF_MARK(s0, ELF_STAGE_PUPIL_GRAD, 1);
+  }
+
+  ELF_CK(cudaStreamWaitEvent(s0, h->ev_join, 0));
+  GatherArgs ga{};
+  ga.G = h->G;
+  ga.pupil = pupil;
+  ga.origin = h->origin;
+  ga.row_xs = h->row_xs;
+  ga.row_cnt = h->row_cnt;
+  ga.row_off = h->row_off;
+  ga.tile_ptr = h->tile_ptr;
+  ga.tile_led = h->tile_led;
+  ga.gH = h->q;
+  ga.psi = h->psi;
+  ga.mu = h->mu_psi;
+  ga.v = h->v_psi;
+  ga.delta = h->delta_psi;
+  ga.g_out = h->g_psi;
+  ga.t_dev = h->t_dev;
+  ga.N = h->N;
+  ga.n = h->n;
+  ga.S = h->S;
+  ga.K = h->K;
+  ga.tiles_x = h->tiles_x;
+  ga.max_list = h->max_list;
+  ga.g1 = (float)h->opt.gamma1;
+  ga.g2 = (float)h->opt.gamma2;
+  ga.eta = (float)h->opt.eta_opt;
+  ga.mode = mode;
+  ELF_MARK(s0, ELF_STAGE_GATHER, 0);
+  ELF_CK(launch_gather(ga, s0));
+  ELF_MARK(s0, ELF_STAGE_GATHER, 1);
+  if (pupil_path) {
+    ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 0);
+    ELF_CK(launch_pupil_update(pa, s0));
+    if (mode == 0)
+      ELF_CK(cudaMemcpyAsync(h->pupil, h->pupil_next, (size_t)h->n * h->n * sizeof(float2),
+                             cudaMemcpyDeviceToDevice, s0));
+    ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 1);
+  }
+  ELF_MARK(s0, ELF_STAGE_COST, 0);
+  ELF_CK(launch_cost_reduce(h->cost_fid, h->K * h->cs, h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
+                            h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, s0));
+  ELF_MARK(s0, ELF_STAGE_COST, 1);
+  ELF_MARK(s0, ELF_STAGE_ITERATION, 1);
+  return ELF_OK;
+}
+
+int build_graph(elf_handle h) {
+  if (h->graph) return ELF_OK;
+  cudaGraph_t g = nullptr;
+  ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_iteration(h, 0, h->cap, h->psi, h->pupil);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (rc != ELF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  size_t nn = 0;
+  h->graph_kernels = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
+      }
+  }
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return ELF_OK;
+}
+
+int check(elf_handle h) {
+  if (!h) return set_error(ELF_EINVAL, "null handle");
+  return ELF_OK;
+}
+
+int copy_out(elf_handle h, void* dst, const void* src, size_t bytes) {
+  ELF_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->user));
+  ELF_CK(cudaStreamSynchronize(h->user));
+  return ELF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int elf_default_options(elf_options* o) {
+  if (!o) return set_error(ELF_EINVAL, "null options");
+  o->fidelity = 0;
+  o->omega_iso = 1;
+  o->learn_pupil = 1;
+  o->pupil_filter = 1;
+  o->alpha = -1.0;
+  o->beta = -1.0;
+  o->gamma1 = 0.9;
+  o->gamma2 = 0.999;
+  o->s0_psi = 1.0;
+  o->s0_pupil = 1e-2;
+  o->eta_opt = 1e-8;
+  o->eta_h = 1e-12;
+  o->tau_fid = 1e-6;
+  o->tau_h = 1e-4;
+  return ELF_OK;
+}
+
+void elf_destroy(elf_handle h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  for (cudaEvent_t ev : h->ev_stage)
+    if (ev) cudaEventDestroy(ev);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  delete h;
+}
+
+static int create_impl(const elf_problem* p, const elf_options* o, void* stream, elf_handle h) {
+  const int n = p->n_lowres, u = p->upsample, K = p->n_led;
+  if (!(n == 16 || n == 32 || n == 64 || n == 128 || n == 256))
+    return set_error(ELF_EINVAL, "n_lowres must be 16, 32, 64, 128 or 256");
+  if (u < 1 || !is_pow2(u) || (long)n * u > 1024 || n * u < 32)
+    return set_error(ELF_EINVAL, "upsample must be a power of two with 32 <= n*u <= 1024");
+  if (K < 1 || K > 65536) return set_error(ELF_EINVAL, "n_led must be in [1, 65536]");
+  if (!p->k_xy) return set_error(ELF_EINVAL, "k_xy is null");
+  if (!(p->na > 0 && p->wavelength_um > 0 && p->pixel_um > 0) || !std::isfinite(p->na) ||
+      !std::isfinite(p->wavelength_um) || !std::isfinite(p->pixel_um))
+    return set_error(ELF_EINVAL, "na, wavelength_um and pixel_um must be finite and positive");
+  if (o) {
+    h->opt = *o;
+  } else {
+    elf_default_options(&h->opt);
+  }
+  const elf_options& op = h->opt;
+  if (!(op.gamma1 >= 0 && op.gamma1 < 1 && op.gamma2 >= 0 && op.gamma2 < 1 && op.tau_fid >= 0 && op.tau_h >= 0 &&
+        op.eta_opt >= 0 && op.eta_h >= 0 && op.s0_psi >= 0 && op.s0_pupil >= 0 && std::isfinite(op.alpha) &&
+        std::isfinite(op.beta) && (op.fidelity == 0 || op.fidelity == 1)))
+    return set_error(ELF_EINVAL, "invalid options");
+  h->n = n;
+  h->u = u;
+  h->N = n * u;
+  h->K = K;
+  const int N = h->N;
+  h->dk = 1.0 / ((double)n * p->pixel_um);
+  // LED offsets (reading A3) and crop windows
+  h->origin_h.resize(K);
+  double best = 1e300;
+  for (int k = 0; k < K; ++k) {
+    const double kx = p->k_xy[2 * k], ky = p->k_xy[2 * k + 1];
+    if (!std::isfinite(kx) || !std::isfinite(ky)) return set_error(ELF_EINVAL, "non-finite k_xy");
+    const double cy = round_half_away(ky / h->dk), cx = round_half_away(kx / h->dk);
+    const double oy = cy + (N / 2 - n / 2), ox = cx + (N / 2 - n / 2);
+    if (oy < 0 || ox < 0 || oy + n > N || ox + n > N)
+      return set_error(ELF_EINVAL, "LED " + std::to_string(k) + ": crop window outside the spectrum");
+    h->origin_h[k] = make_int2((int)oy, (int)ox);
+    const double r2 = kx * kx + ky * ky;
+    if (r2 < best) {
+      best = r2;
+      h->centre = k;
+    }
+  }
+  // pupil support (reading A4), rows are contiguous runs of a disc
+  const double cut = (p->na / p->wavelength_um) * (p->na / p->wavelength_um);
+  std::vector<int> xs(n, 0), cnt(n, 0), off(n, 0), sidx_map(n * n, -1), supy, supx;
+  int S = 0, Blo = -1, Bhi = -1;
+  for (int jy = 0; jy < n; ++jy) {
+    off[jy] = S;
+    for (int jx = 0; jx < n; ++jx) {
+      const double a = jx - n / 2, b = jy - n / 2;
+      const double rho2 = (a * a + b * b) * h->dk * h->dk;
+      if (rho2 <= cut) {
+        if (cnt[jy] == 0) xs[jy] = jx;
+        if (jx != xs[jy] + cnt[jy]) return set_error(ELF_EINVAL, "support row is not contiguous");
+        cnt[jy]++;
+        sidx_map[jy * n + jx] = S++;
+        supy.push_back(jy);
+        supx.push_back(jx);
+        h->sidx_h.push_back(jy * n + jx);
+      }
+    }
+    if (cnt[jy] > 0) {
+      if (Blo < 0) Blo = jy;
+      if (Bhi >= 0 && Bhi != jy - 1) return set_error(ELF_EINVAL, "support rows are not contiguous");
+      Bhi = jy;
+    }
+  }
+  if (S == 0) return set_error(ELF_EINVAL, "empty pupil support (NA/wavelength smaller than one spectral pixel)");
+  h->S = S;
+  h->Blo = Blo;
+  h->nb = Bhi - Blo + 1;
+  h->cs = tile_cluster_size(n);
+  h->rowsA = (h->nb + h->cs - 1) / h->cs;
+  h->Q = pupil_chunks(K, S);
+  h->hblocks = hess_blocks(N);
+  // per-tile LED lists for the gather (ascending LED order)
+  h->tiles_x = N / kGatherTile;
+  std::vector<int> tptr(1, 0), tled;
+  for (int ty = 0; ty < h->tiles_x; ++ty)
+    for (int tx = 0; tx < h->tiles_x; ++tx) {
+      const int y0 = ty * kGatherTile, y1 = y0 + kGatherTile - 1, x0 = tx * kGatherTile, x1 = x0 + kGatherTile - 1;
+      int c = 0;
+      for (int k = 0; k < K; ++k) {
+        const int by0 = h->origin_h[k].x + Blo, by1 = h->origin_h[k].x + Bhi;
+        const int bx0 = h->origin_h[k].y + Blo, bx1 = h->origin_h[k].y + Bhi;  // the disc is symmetric
+        if (by1 < y0 || by0 > y1 || bx1 < x0 || bx0 > x1) continue;
+        tled.push_back(k);
+        ++c;
+      }
+      if (c > h->max_list) h->max_list = c;
+      tptr.push_back((int)tled.size());
+    }
+  if (h->max_list > 1024) return set_error(ELF_EINVAL, "more than 1024 LEDs overlap one 32x32 spectrum tile");
+  // Gaussian 3x3, sigma = 1 px, normalised (note under Algorithm 1)
+  const double e = std::exp(-0.5), tot = 1.0 + 2.0 * e;
+  h->gw0 = (float)(1.0 / tot);
+  h->gw1 = (float)(e / tot);
+
+  // streams and events
+  h->user = static_cast<cudaStream_t>(stream);
+  ELF_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  ELF_CK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));
+
+  // device memory
+  int rc;
+  const size_t A = (size_t)N * N, B = (size_t)n * n;
+  if ((rc = upload(h, &h->origin, h->origin_h))) return rc;
+  if ((rc = upload(h, &h->row_xs, xs))) return rc;
+  if ((rc = upload(h, &h->row_cnt, cnt))) return rc;
+  if ((rc = upload(h, &h->row_off, off))) return rc;
+  if ((rc = upload(h, &h->sup_y, supy))) return rc;
+  if ((rc = upload(h, &h->sup_x, supx))) return rc;
+  if ((rc = upload(h, &h->sidx_map, sidx_map))) return rc;
+  if ((rc = upload(h, &h->tile_ptr, tptr))) return rc;
+  if ((rc = upload(h, &h->tile_led, tled))) return rc;
+  if ((rc = upload(h, &h->tw_n, twiddles(n)))) return rc;
+  if ((rc = upload(h, &h->tw_N, twiddles(N)))) return rc;
+  if ((rc = dalloc(h, &h->I, (size_t)K * B))) return rc;
+  if ((rc = dalloc(h, &h->psi, A))) return rc;
+  if ((rc = dalloc(h, &h->mu_psi, A))) return rc;
+  if ((rc = dalloc(h, &h->v_psi, A))) return rc;
+  if ((rc = dalloc(h, &h->delta_psi, A))) return rc;
+  if ((rc = dalloc(h, &h->pupil, B))) return rc;
+  if ((rc = dalloc(h, &h->pupil_next, B))) return rc;
+  if ((rc = dalloc(h, &h->mu_p, B))) return rc;
+  if ((rc = dalloc(h, &h->v_p, B))) return rc;
+  if ((rc = dalloc(h, &h->delta_p, B))) return rc;
+  if ((rc = dalloc(h, &h->G, (size_t)K * S))) return rc;
+  if ((rc = dalloc(h, &h->ot, A))) return rc;
+  if ((rc = dalloc(h, &h->q, A))) return rc;
+  if ((rc = dalloc(h, &h->small, B))) return rc;
+  if ((rc = dalloc(h, &h->part, (size_t)h->Q * S))) return rc;
+  if ((rc = dalloc(h, &h->psi_eval, A))) return rc;
+  if ((rc = dalloc(h, &h->pupil_eval, B))) return rc;
+  if ((rc = dalloc(h, &h->g_psi, A))) return rc;
+  if ((rc = dalloc(h, &h->g_p, B))) return rc;
+  if ((rc = dalloc(h, &h->pupil_unit, B))) return rc;
+  if ((rc = dalloc(h, &h->cost_fid, (size_t)K * h->cs))) return rc;
+  if ((rc = dalloc(h, &h->cost_h, (size_t)2 * h->hblocks))) return rc;
+  if ((rc = dalloc(h, &h->ring, (size_t)3 * kCostRing))) return rc;
+  if ((rc = dalloc(h, &h->weights, 2))) return rc;
+  if ((rc = dalloc(h, &h->alpha_part, (size_t)K))) return rc;
+  if ((rc = dalloc(h, &h->out3, 3))) return rc;
+  if ((rc = dalloc(h, &h->t_dev, 1))) return rc;
+  if ((rc = dalloc(h, &h->flag, 1))) return rc;
+  ELF_CK(prepare_tile(n, h->rowsA));
+  ELF_CK(prepare_fft(n));
+  ELF_CK(prepare_fft(N));
+  ELF_CK(launch_support_pupil(h->pupil_unit, h->sidx_map, n, h->user));
+  ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), h->user));
+  ELF_CK(cudaMemsetAsync(h->ring, 0, 3 * kCostRing * sizeof(double), h->user));
+  ELF_CK(cudaStreamSynchronize(h->user));
+  return ELF_OK;
+}
+
+int elf_create(const elf_problem* p, const elf_options* o, void* stream, elf_handle* out) {
+  if (!p || !out) return set_error(ELF_EINVAL, "null argument");
+  *out = nullptr;
+  elf_handle h = new elf_handle_s();
+  const int rc = create_impl(p, o, stream, h);
+  if (rc != ELF_OK) {
+    elf_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return ELF_OK;
+}
+
+int elf_set_measurements(elf_handle h, const float* I, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!I) return set_error(ELF_EINVAL, "null measurements");
+  (void)is_device;
+  const size_t B = (size_t)h->n * h->n, A = (size_t)h->N * h->N;
+  cudaStream_t s = h->user;
+  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * B * sizeof(float), cudaMemcpyDefault, s));
+  ELF_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+  ELF_CK(launch_count_nonfinite(h->I, (size_t)h->K * B, h->flag, s));
+  int bad = 0;
+  ELF_CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ELF_CK(cudaStreamSynchronize(s));
+  if (bad) {
+    h->have_meas = false;
+    return set_error(ELF_EINVAL, "measurements contain NaN or Inf");
+  }
+  // alpha = beta (Eqs. 16-17) and the initial state (reading A9)
+  ELF_CK(launch_alpha(h->I, h->K, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
+  ELF_CK(launch_init_small(h->I + (size_t)h->centre * B, h->small, h->n, s));
+  ELF_CK(launch_fft2(h->small, h->n, false, h->tw_n, s));
+  ELF_CK(launch_embed(h->small, h->psi, h->n, h->N, h->origin_h[h->centre].x, h->origin_h[h->centre].y,
+                      (float)(h->u * h->u), s));
+  ELF_CK(launch_fill_f2(h->mu_psi, A, make_float2(0.f, 0.f), s));
+  ELF_CK(launch_fill_f(h->v_psi, A, 0.f, s));
+  ELF_CK(launch_fill_f(h->delta_psi, A, (float)(h->opt.s0_psi * h->opt.s0_psi), s));
+  ELF_CK(launch_support_pupil(h->pupil, h->sidx_map, h->n, s));
+  ELF_CK(launch_fill_f2(h->mu_p, B, make_float2(0.f, 0.f), s));
+  ELF_CK(launch_fill_f(h->v_p, B, 0.f, s));
+  ELF_CK(launch_fill_f(h->delta_p, B, (float)(h->opt.s0_pupil * h->opt.s0_pupil), s));
+  ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), s));
+  ELF_CK(cudaStreamSynchronize(s));
+  h->have_meas = true;
+  return ELF_OK;
+}
+
+int elf_step(elf_handle h, int n_iter) {
+  if (int rc = check(h)) return rc;
+  if (!h->have_meas) return set_error(ELF_ESTATE, "elf_step before elf_set_measurements");
+  if (n_iter < 0) return set_error(ELF_EINVAL, "negative n_iter");
+  if (int rc = build_graph(h)) return rc;
+  for (int i = 0; i < n_iter; ++i) ELF_CK(cudaGraphLaunch(h->graph, h->user));
+  return ELF_OK;
+}
+
+int elf_get_spectrum(elf_handle h, float* psi, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!psi) return set_error(ELF_EINVAL, "null output");
+  (void)is_device;
+  return copy_out(h, psi, h->psi, (size_t)h->N * h->N * sizeof(float2));
+}
+
+int elf_get_pupil(elf_handle h, float* pupil, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!pupil) return set_error(ELF_EINVAL, "null output");
+  (void)is_device;
+  return copy_out(h, pupil, h->pupil, (size_t)h->n * h->n * sizeof(float2));
+}
+
+int elf_get_object(elf_handle h, float* obj, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!obj) return set_error(ELF_EINVAL, "null output");
+  (void)is_device;
+  const size_t A = (size_t)h->N * h->N;
+  ELF_CK(cudaMemcpyAsync(h->ot, h->psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->user));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user));
+  ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
+  return copy_out(h, obj, h->ot, A * sizeof(float2));
+}
+
+int elf_get_costs(elf_handle h, double* out, int max_iter) {
+  if (int rc = check(h)) return rc;
+  if (!out || max_iter < 0) return set_error(ELF_EINVAL, "bad output");
+  int t = 0;
+  ELF_CK(cudaMemcpyAsync(&t, h->t_dev, sizeof(int), cudaMemcpyDeviceToHost, h->user));
+  ELF_CK(cudaStreamSynchronize(h->user));
+  int count = t < max_iter ? t : max_iter;
+  if (count > kCostRing) count = kCostRing;
+  std::vector<double> ring(3 * kCostRing);
+  ELF_CK(cudaMemcpy(ring.data(), h->ring, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < count; ++i) {
+    const int it = t - count + i;
+    std::memcpy(out + 3 * i, ring.data() + 3 * (it % kCostRing), 3 * sizeof(double));
+  }
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (!std::isfinite(out[3 * i + j])) return set_error(ELF_ENUMERIC, "non-finite cost");
+  return count;
+}
+
+int elf_get_state(elf_handle h, const elf_state* st, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!st) return set_error(ELF_EINVAL, "null state");
+  (void)is_device;
+  const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
+  cudaStream_t s = h->user;
+  struct {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } cp[] = {{st->psi, h->psi, A * 8},       {st->mu_psi, h->mu_psi, A * 8},    {st->v_psi, h->v_psi, A * 4},
+            {st->delta_psi, h->delta_psi, A * 4}, {st->pupil, h->pupil, B * 8}, {st->mu_pupil, h->mu_p, B * 8},
+            {st->v_pupil, h->v_p, B * 4},   {st->delta_pupil, h->delta_p, B * 4}};
+  for (auto& c : cp)
+    if (c.dst) ELF_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, s));
+  int t = 0;
+  double w[2] = {0, 0};
+  ELF_CK(cudaMemcpyAsync(&t, h->t_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ELF_CK(cudaMemcpyAsync(w, h->weights, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ELF_CK(cudaStreamSynchronize(s));
+  elf_state* mst = const_cast<elf_state*>(st);
+  mst->t = t;
+  mst->alpha = w[0];
+  mst->beta = w[1];
+  return ELF_OK;
+}
+
+int elf_set_state(elf_handle h, const elf_state* st, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!st || !st->psi || !st->mu_psi || !st->v_psi || !st->delta_psi || !st->pupil || !st->mu_pupil ||
+      !st->v_pupil || !st->delta_pupil)
+    return set_error(ELF_EINVAL, "incomplete state");
+  if (st->t < 0 || !std::isfinite(st->alpha) || !std::isfinite(st->beta) || st->alpha < 0 || st->beta < 0)
+    return set_error(ELF_EINVAL, "invalid t, alpha or beta");
+  if (!h->have_meas) return set_error(ELF_ESTATE, "elf_set_state before elf_set_measurements");
+  (void)is_device;
+  const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
+  cudaStream_t s = h->user;
+  ELF_CK(cudaMemcpyAsync(h->psi, st->psi, A * 8, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->mu_psi, st->mu_psi, A * 8, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->v_psi, st->v_psi, A * 4, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->delta_psi, st->delta_psi, A * 4, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->pupil, st->pupil, B * 8, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->mu_p, st->mu_pupil, B * 8, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->v_p, st->v_pupil, B * 4, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->delta_p, st->delta_pupil, B * 4, cudaMemcpyDefault, s));
+  const int t = st->t;
+  const double w[2] = {st->alpha, st->beta};
+  ELF_CK(cudaMemcpyAsync(h->t_dev, &t, sizeof(int), cudaMemcpyHostToDevice, s));
+  ELF_CK(cudaMemcpyAsync(h->weights, w, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  ELF_CK(cudaStreamSynchronize(s));
+  return ELF_OK;
+}
+
+int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs3, float* g_psi, float* g_pupil,
+                  int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!psi || !pupil) return set_error(ELF_EINVAL, "null psi or pupil");
+  if (!h->have_meas) return set_error(ELF_ESTATE, "elf_cost_grad before elf_set_measurements");
+  (void)is_device;
+  const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
+  cudaStream_t s = h->user;
+  ELF_CK(cudaMemcpyAsync(h->psi_eval, psi, A * 8, cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->pupil_eval, pupil, B * 8, cudaMemcpyDefault, s));
+  if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval)) return rc;
+  if (g_psi) ELF_CK(cudaMemcpyAsync(g_psi, h->g_psi, A * 8, cudaMemcpyDefault, s));
+  if (g_pupil) ELF_CK(cudaMemcpyAsync(g_pupil, h->g_p, B * 8, cudaMemcpyDefault, s));
+  double c[3];
+  ELF_CK(cudaMemcpyAsync(c, h->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ELF_CK(cudaStreamSynchronize(s));
+  if (costs3) std::memcpy(costs3, c, sizeof(c));
+  for (double v : c)
+    if (!std::isfinite(v)) return set_error(ELF_ENUMERIC, "non-finite cost");
+  return ELF_OK;
+}
+
+int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!obj || !I_out) return set_error(ELF_EINVAL, "null argument");
+  const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
+  cudaStream_t s = h->user;
+  // Psi = fftshift(DFT_N(O)) = DFT_N((-1)^(x+y) O)
+  ELF_CK(cudaMemcpyAsync(h->psi_eval, obj, A * 8, cudaMemcpyDefault, s));
+  ELF_CK(launch_sign_scale(h->psi_eval, h->psi_eval, h->N, 1.f, s));
+  ELF_CK(launch_fft2(h->psi_eval, h->N, false, h->tw_N, s));
+  float* dst = I_out;
+  float* staging = nullptr;
+  if (!is_device) {
+    ELF_CK(cudaMalloc(&staging, (size_t)h->K * B * sizeof(float)));
+    dst = staging;
+  }
+  TileArgs ta{};
+  ta.psi = h->psi_eval;
+  ta.pupil = h->pupil_unit;
+  ta.origin = h->origin;
+  ta.row_xs = h->row_xs;
+  ta.row_cnt = h->row_cnt;
+  ta.row_off = h->row_off;
+  ta.tw = h->tw_n;
+  ta.I_out = dst;
+  ta.costpart = h->cost_fid;
+  ta.N = h->N;
+  ta.K = h->K;
+  ta.S = h->S;
+  ta.Blo = h->Blo;
+  ta.nb = h->nb;
+  ta.rowsA = h->rowsA;
+  ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
+  ta.mode = 1;
+  cudaError_t e = launch_tile(ta, h->n, s);
+  if (e == cudaSuccess && staging) e = cudaMemcpyAsync(I_out, staging, (size_t)h->K * B * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (staging) cudaFree(staging);
+  if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("elf_simulate: ") + cudaGetErrorString(e));
+  return ELF_OK;
+}
+
+int elf_get_tile_grads(elf_handle h, float* G_out, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!G_out) return set_error(ELF_EINVAL, "null output");
+  (void)is_device;
+  return copy_out(h, G_out, h->G, (size_t)h->K * h->S * sizeof(float2));
+}
+
+int elf_get_support(elf_handle h, int* idx) {
+  if (int rc = check(h)) return rc;
+  if (idx) std::memcpy(idx, h->sidx_h.data(), h->sidx_h.size() * sizeof(int));
+  return h->S;
+}
+
+int elf_get_weights(elf_handle h, double* alpha, double* beta) {
+  if (int rc = check(h)) return rc;
+  double w[2];
+  ELF_CK(cudaMemcpyAsync(w, h->weights, sizeof(w), cudaMemcpyDeviceToHost, h->user));
+  ELF_CK(cudaStreamSynchronize(h->user));
+  if (alpha) *alpha = w[0];
+  if (beta) *beta = w[1];
+  return ELF_OK;
+}
+
+int elf_set_tracing(elf_handle h, int enable) {
+  if (int rc = check(h)) return rc;
+  const bool en = enable != 0;
+  if (en != h->tracing && h->graph) {
+    ELF_CK(cudaStreamSynchronize(h->user));
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->tracing = en;
+  return ELF_OK;
+}
+
+int elf_get_stage_times(elf_handle h, float* ms, int max_stages) {
+  if (int rc = check(h)) return rc;
+  if (!ms || max_stages < 0) return set_error(ELF_EINVAL, "bad output");
+  if (!h->tracing) return set_error(ELF_ESTATE, "tracing is off");
+  ELF_CK(cudaStreamSynchronize(h->user));
+  const int n = max_stages < ELF_NSTAGES ? max_stages : ELF_NSTAGES;
+  for (int i = 0; i < n; ++i) {
+    float t = -1.f;
+    if (cudaEventElapsedTime(&t, h->ev_stage[2 * i], h->ev_stage[2 * i + 1]) != cudaSuccess) t = -1.f;
+    ms[i] = t;
+  }
+  cudaGetLastError();  // stages that never ran leave a benign "not ready" error behind
+  return n;
+}
+
+int elf_graph_kernel_count(elf_handle h) {
+  if (int rc = check(h)) return rc;
+  if (int rc = build_graph(h)) return rc;
+  return h->graph_kernels;
+}
+
+const char* elf_strerror(int code) {
+  switch (code) {
+    case ELF_OK: return "ok";
+    case ELF_EINVAL: return "invalid argument";
+    case ELF_ENOMEM: return "out of device memory";
+    case ELF_ECUDA: return "CUDA error";
+    case ELF_ENUMERIC: return "non-finite cost";
+    case ELF_ETIMEOUT: return "timeout";
+    case ELF_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* elf_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal interfaces between the host API (elfpie_api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace elf {
+
+constexpr int kGatherTile = 32;   // spectrum tile side of the gather lists
+constexpr int kCostRing = 4096;   // iterations kept in the cost ring buffer
+
+// ---------------------------------------------------------------- tile kernel
+// One cluster of CS CTAs per LED runs Eqs. 1, 5/4, 12, 11/10 and F_B^H of Eq. 9.
+struct TileArgs {
+  const float2* psi;      // N x N centred spectrum
+  const float2* pupil;    // n x n centred pupil (read on the support only)
+  const float* meas;      // K x n x n measured intensities (gradient mode)
+  const int2* origin;     // K crop origins (.x = row, .y = col)
+  const int* row_xs;      // n: first support column of each pupil row (or 0)
+  const int* row_cnt;     // n: support pixels in each pupil row
+  const int* row_off;     // n: compact index of the first support pixel of each row
+  const float2* tw;       // n twiddles e^{-2 pi i k / n}
+  float2* G;              // K x S tile gradients on the support (gradient mode)
+  double* costpart;       // K x CS fidelity cost partials
+  float* I_out;           // K x n x n predicted intensities (simulate mode)
+  int N, K, S, Blo, nb, rowsA;
+  float scale;            // 1 / (u^2 n^2)
+  float tau, eta;
+  int fidelity, iso;
+  int mode;               // 0 = gradient, 1 = simulate |o|^2
+};
+int tile_cluster_size(int n);
+size_t tile_smem_bytes(int n, int cs, int rowsA);
+cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
+cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------- big FFTs
+// 2D transforms of an L x L array: rows pass then columns pass, unnormalised.
+cudaError_t prepare_fft(int L);               // sets kernel attributes; call outside capture
+cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s);
+// dst[y][x] = (-1)^(x+y) * scale * src[y][x] over an L x L array (src may equal dst).
+cudaError_t launch_sign_scale(const float2* src, float2* dst, int L, float scale, cudaStream_t s);
+
+// ---------------------------------------------------------------- Hessian branch
+struct HessArgs {
+  const float2* ot;       // unnormalised IDFT_N(Psi) (no shift applied)
+  float2* q;              // out: (-1)^(x+y) q / A, ready for the forward DFT
+  double* costpart;       // [blocks][2] (L_A, L_Phi) partials
+  const double* weights;  // device [alpha, beta]
+  int N;
+  float invA, tau, eta;
+  int iso;
+};
+int hess_blocks(int N);
+cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- gather + AdaBelief
+struct GatherArgs {
+  const float2* G;        // K x S
+  const float2* pupil;    // n x n
+  const int2* origin;     // K
+  const int* row_xs; const int* row_cnt; const int* row_off;
+  const int* tile_ptr;    // tiles + 1
+  const int* tile_led;    // LED lists per spectrum tile, ascending
+  const float2* gH;       // N x N Hessian gradient (may be null)
+  float2* psi; float2* mu; float* v; float* delta;   // state (update mode)
+  float2* g_out;          // gradient output (gradient mode)
+  const int* t_dev;
+  int N, n, S, K, tiles_x, max_list;
+  float g1, g2, eta;
+  int mode;               // 0 = AdaBelief update, 1 = write g
+};
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- pupil
+struct PupilArgs {
+  const float2* G; const float2* psi; const int2* origin;
+  const int* sup_y; const int* sup_x; const int* sidx_map;   // S, S, n*n
+  float2* part;           // Q x S
+  const float2* pupil;    // P^t
+  float2* pupil_next;     // P^{t+1}
+  float2* mu; float* v; float* delta;
+  float2* g_out;          // gradient mode output (n x n)
+  const int* t_dev;
+  int N, n, S, K, Q, filter;
+  float w0, w1;           // 1D Gaussian weights (centre, side), normalised
+  float g1, g2, eta;
+  int mode;               // 0 = update, 1 = write g
+};
+int pupil_chunks(int K, int S);
+cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s);
+cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- reductions / setup
+cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring,
+                               int* t_dev, double* out3, int advance, cudaStream_t s);
+int alpha_blocks(int K, int n);
+cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
+                         double fixed_alpha, double fixed_beta, cudaStream_t s);
+cudaError_t launch_init_small(const float* I_c, float2* small, int n, cudaStream_t s);
+cudaError_t launch_embed(const float2* small, float2* psi, int n, int N, int oy, int ox, float gain,
+                         cudaStream_t s);
+cudaError_t launch_fill_f2(float2* p, size_t count, float2 value, cudaStream_t s);
+cudaError_t launch_fill_f(float* p, size_t count, float value, cudaStream_t s);
+cudaError_t launch_support_pupil(float2* p, const int* sidx_map, int n, cudaStream_t s);
+cudaError_t launch_count_nonfinite(const float* x, size_t count, int* flag, cudaStream_t s);
+
+}  // namespace elf

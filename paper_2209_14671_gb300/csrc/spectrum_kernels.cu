@@ -1,0 +1,469 @@
+// Spectrum-sized kernels of one Elfpie iteration and its set-up:
+//   hessian_kernel   Eqs. 6-7 costs and the object-domain factors of Eqs. 13-14
+//   gather_kernel    Eq. 9's sum over LEDs (fixed ascending order, no atomics)
+//                    fused with the Eq. 19 update of Psi (g = Eq. 15)
+//   pupil kernels    Eq. 18 in fixed LED chunks, the 3x3 Gaussian smoothing of P
+//                    (note under Algorithm 1) and Eq. 19 for P
+//   cost_reduce      Eq. 8's three terms in FP64, fixed order
+//   alpha kernels    Eqs. 16-17 in FP64, fixed order
+//   init kernels     the initial state of elf_set_measurements
+#include "fft.cuh"
+#include "internal.cuh"
+
+namespace elf {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double block_sum_double(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) s += red[i];
+  return s;  // valid in thread 0
+}
+
+// Smoothed L1 of a 3-vector (reading A7): cost and omega = h / max(|h|, tau).
+__device__ __forceinline__ float huber3(float& h0, float& h1, float& h2, float tau, int iso) {
+  if (iso) {
+    const float nrm = sqrtf(h0 * h0 + h1 * h1 + h2 * h2);
+    const float den = fmaxf(nrm, tau);
+    h0 /= den;
+    h1 /= den;
+    h2 /= den;
+    return (nrm >= tau) ? nrm : nrm * nrm / (2.f * tau) + 0.5f * tau;
+  }
+  float c = 0.f;
+  float* hs[3] = {&h0, &h1, &h2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float a = fabsf(*hs[i]);
+    c += (a >= tau) ? a : a * a / (2.f * tau) + 0.5f * tau;
+    *hs[i] /= fmaxf(a, tau);
+  }
+  return c;
+}
+
+// ------------------------------------------------------------------ Hessian (Eqs. 6-7, 13-14)
+constexpr int HT = 32;            // output tile side
+constexpr int HA = HT + 4;        // amplitude/phase tile with a 2-pixel halo
+constexpr int HW = HT + 2;        // omega tile with a 1-pixel halo
+
+__global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
+  __shared__ float s_a[HA][HA + 1];
+  __shared__ float s_p[HA][HA + 1];
+  __shared__ float s_w[6][HW][HW + 1];
+  __shared__ double red[8];
+  const int N = a.N;
+  const int tx0 = blockIdx.x * HT, ty0 = blockIdx.y * HT;
+  const int tid = threadIdx.x;
+  const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
+
+  // O = (-1)^(x+y) Ot / A; amplitude and phase (atan2, reading A12)
+  for (int i = tid; i < HA * HA; i += 256) {
+    const int ly = i / HA, lx = i - ly * HA;
+    const int y = ty0 - 2 + ly, x = tx0 - 2 + lx;
+    float am = 0.f, ph = 0.f;
+    if (y >= 0 && y < N && x >= 0 && x < N) {
+      float2 o = a.ot[(size_t)y * N + x];
+      const float sg = ((x + y) & 1) ? -a.invA : a.invA;
+      o.x *= sg;
+      o.y *= sg;
+      am = sqrtf(cabs2(o));
+      ph = atan2f(o.y, o.x);
+    }
+    s_a[ly][lx] = am;
+    s_p[ly][lx] = ph;
+  }
+  __syncthreads();
+
+  // omega = H f / max(|H f|, tau) on the interior [1, N-2]^2, zero elsewhere
+  double ca = 0.0, cp = 0.0;
+  const float r2 = 1.41421356237309505f;
+  for (int i = tid; i < HW * HW; i += 256) {
+    const int ly = i / HW, lx = i - ly * HW;
+    const int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
+    const int cy = ly + 1, cx = lx + 1;  // centre in the HA tile
+    float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (y >= 1 && y <= N - 2 && x >= 1 && x <= N - 2) {
+      float h0 = s_a[cy][cx - 1] - 2.f * s_a[cy][cx] + s_a[cy][cx + 1];
+      float h1 = s_a[cy - 1][cx] - 2.f * s_a[cy][cx] + s_a[cy + 1][cx];
+      float h2 = r2 * 0.25f * (s_a[cy + 1][cx + 1] - s_a[cy + 1][cx - 1] - s_a[cy - 1][cx + 1] + s_a[cy - 1][cx - 1]);
+      const float fa = huber3(h0, h1, h2, a.tau, a.iso);
+      float g0 = s_p[cy][cx - 1] - 2.f * s_p[cy][cx] + s_p[cy][cx + 1];
+      float g1 = s_p[cy - 1][cx] - 2.f * s_p[cy][cx] + s_p[cy + 1][cx];
+      float g2 = r2 * 0.25f * (s_p[cy + 1][cx + 1] - s_p[cy + 1][cx - 1] - s_p[cy - 1][cx + 1] + s_p[cy - 1][cx - 1]);
+      const float fp = huber3(g0, g1, g2, a.tau, a.iso);
+      w[0] = h0; w[1] = h1; w[2] = h2; w[3] = g0; w[4] = g1; w[5] = g2;
+      if (ly >= 1 && ly <= HT && lx >= 1 && lx <= HT) {  // owned pixel
+        ca += (double)fa;
+        cp += (double)fp;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_w[k][ly][lx] = w[k];
+  }
+  __syncthreads();
+
+  // q = alpha O/(2 max(a,eta)) H^T omega_a + beta (i/2) O/(a^2+eta) H^T omega_phi
+  for (int i = tid; i < HT * HT; i += 256) {
+    const int ly = i / HT, lx = i - ly * HT;
+    const int y = ty0 + ly, x = tx0 + lx;
+    if (y >= N || x >= N) continue;
+    const int wy = ly + 1, wx = lx + 1;
+    float t[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const int k = 3 * f;
+      const float dxx = s_w[k][wy][wx - 1] - 2.f * s_w[k][wy][wx] + s_w[k][wy][wx + 1];
+      const float dyy = s_w[k + 1][wy - 1][wx] - 2.f * s_w[k + 1][wy][wx] + s_w[k + 1][wy + 1][wx];
+      const float dxy = s_w[k + 2][wy - 1][wx - 1] - s_w[k + 2][wy - 1][wx + 1] - s_w[k + 2][wy + 1][wx - 1] +
+                        s_w[k + 2][wy + 1][wx + 1];
+      t[f] = dxx + dyy + r2 * 0.25f * dxy;
+    }
+    const float am = s_a[ly + 2][lx + 2];
+    float2 o = a.ot[(size_t)y * N + x];
+    const float sg = ((x + y) & 1) ? -a.invA : a.invA;
+    o.x *= sg;
+    o.y *= sg;
+    const float ka = alpha * t[0] / (2.f * fmaxf(am, a.eta));
+    const float kp = beta * 0.5f * t[1] / (am * am + a.eta);
+    // ka O + i kp O, then the forward-shift sign and 1/A
+    float2 q = make_float2(ka * o.x - kp * o.y, ka * o.y + kp * o.x);
+    a.q[(size_t)y * N + x] = cscale(q, sg);
+  }
+  const double sa = block_sum_double(ca, red);
+  const double sp = block_sum_double(cp, red);
+  if (tid == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    a.costpart[2 * b] = sa;
+    a.costpart[2 * b + 1] = sp;
+  }
+}
+
+int hess_blocks(int N) { return ((N + HT - 1) / HT) * ((N + HT - 1) / HT); }
+
+cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s) {
+  const int t = (a.N + HT - 1) / HT;
+  hessian_kernel<<<dim3(t, t), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gather + AdaBelief (Eqs. 9, 15, 19)
+__device__ __forceinline__ void bias_corrections(const int* t_dev, float g1, float g2, float* s_bc) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int t = *t_dev + 1;
+    s_bc[0] = (float)(1.0 / (1.0 - pow((double)g1, (double)t)));
+    s_bc[1] = (float)(1.0 / (1.0 - pow((double)g2, (double)t)));
+  }
+}
+
+// Eq. 19 for one complex parameter; returns the increment Delta.
+__device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v, float& delta, float g1, float g2,
+                                                 float eta, float bc1, float bc2) {
+  mu = make_float2(g1 * mu.x + (1.f - g1) * g.x, g1 * mu.y + (1.f - g1) * g.y);
+  const float ex = mu.x - g.x, ey = mu.y - g.y;
+  v = g2 * v + (1.f - g2) * (ex * ex + ey * ey);
+  const float vhat = v * bc2;
+  const float k = (sqrtf(delta) + eta) / (sqrtf(vhat) + eta);
+  const float2 d = make_float2(k * (g1 * mu.x * bc1 + (1.f - g1) * g.x), k * (g1 * mu.y * bc1 + (1.f - g1) * g.y));
+  delta = g1 * delta + (1.f - g1) * cabs2(d);
+  return d;
+}
+
+constexpr int kMaxTileList = 1024;
+
+__global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
+  __shared__ int s_led[kMaxTileList];
+  __shared__ int2 s_org[kMaxTileList];
+  __shared__ float s_bc[2];
+  extern __shared__ int s_rows[];   // row_xs, row_cnt, row_off (n each)
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int tile = blockIdx.y * a.tiles_x + blockIdx.x;
+  const int l0 = a.tile_ptr[tile], cnt = a.tile_ptr[tile + 1] - l0;
+  for (int i = tid; i < cnt; i += 256) {
+    const int led = a.tile_led[l0 + i];
+    s_led[i] = led;
+    s_org[i] = a.origin[led];
+  }
+  for (int i = tid; i < a.n; i += 256) {
+    s_rows[i] = a.row_xs[i];
+    s_rows[a.n + i] = a.row_cnt[i];
+    s_rows[2 * a.n + i] = a.row_off[i];
+  }
+  if (a.mode == 0) bias_corrections(a.t_dev, a.g1, a.g2, s_bc);
+  __syncthreads();
+  const int x = blockIdx.x * kGatherTile + threadIdx.x;
+  for (int r = threadIdx.y; r < kGatherTile; r += 8) {
+    const int y = blockIdx.y * kGatherTile + r;
+    const size_t k = (size_t)y * a.N + x;
+    float2 g = a.gH ? a.gH[k] : make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = 0; i < cnt; ++i) {
+      const int2 o = s_org[i];
+      const int jy = y - o.x, jx = x - o.y;
+      if ((unsigned)jy >= (unsigned)a.n) continue;
+      const int d = jx - s_rows[jy];
+      if ((unsigned)d >= (unsigned)s_rows[a.n + jy]) continue;
+      const float2 p = a.pupil[jy * a.n + jx];
+      const float2 gt = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
+      acc = cadd(acc, cconjmul(p, gt));
+    }
+    g = cadd(g, acc);
+    if (a.mode == 1) {
+      a.g_out[k] = g;
+      continue;
+    }
+    float2 mu = a.mu[k];
+    float v = a.v[k], dl = a.delta[k];
+    const float2 d = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, s_bc[0], s_bc[1]);
+    const float2 p = a.psi[k];
+    a.psi[k] = csub(p, d);
+    a.mu[k] = mu;
+    a.v[k] = v;
+    a.delta[k] = dl;
+  }
+}
+
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
+  if (a.max_list > kMaxTileList) return cudaErrorInvalidValue;
+  dim3 grid(a.tiles_x, a.tiles_x), block(32, 8);
+  gather_kernel<<<grid, block, 3 * a.n * sizeof(int), s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pupil (Eq. 18, Eq. 19, Gaussian filter)
+int pupil_chunks(int K, int S) {
+  // enough (support pixel, LED chunk) pairs to fill the GPU, chunks of >= 4 LEDs
+  int q = (4 * 152 * 256 + S - 1) / (S > 0 ? S : 1);
+  if (q > K / 4) q = K / 4;
+  if (q < 1) q = 1;
+  return q;
+}
+
+__global__ void __launch_bounds__(256) pupil_partial_kernel(const PupilArgs a) {
+  const int s = blockIdx.x * 256 + threadIdx.x;
+  if (s >= a.S) return;
+  const int q = blockIdx.y;
+  const int kc = (a.K + a.Q - 1) / a.Q;
+  const int k0 = q * kc, k1 = min(a.K, k0 + kc);
+  const int jy = a.sup_y[s], jx = a.sup_x[s];
+  float2 acc = make_float2(0.f, 0.f);
+  for (int k = k0; k < k1; ++k) {
+    const int2 o = a.origin[k];
+    const float2 ps = a.psi[(size_t)(o.x + jy) * a.N + o.y + jx];
+    acc = cadd(acc, cconjmul(ps, a.G[(size_t)k * a.S + s]));
+  }
+  a.part[(size_t)q * a.S + s] = acc;
+}
+
+__global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
+  __shared__ float s_bc[2];
+  if (a.mode == 0) bias_corrections(a.t_dev, a.g1, a.g2, s_bc);
+  __syncthreads();
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  const int n = a.n;
+  if (j >= n * n) return;
+  const int sidx = a.sidx_map[j];
+  float2 g = make_float2(0.f, 0.f);
+  if (sidx >= 0)
+    for (int q = 0; q < a.Q; ++q) g = cadd(g, a.part[(size_t)q * a.S + sidx]);
+  if (a.mode == 1) {
+    a.g_out[j] = g;
+    return;
+  }
+  const int jy = j / n, jx = j - jy * n;
+  float2 base;
+  if (a.filter) {
+    base = make_float2(0.f, 0.f);
+    const float w[3] = {a.w1, a.w0, a.w1};
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = jy + dy, xx = jx + dx;
+        if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
+        base = cadd(base, cscale(a.pupil[yy * n + xx], w[dy + 1] * w[dx + 1]));
+      }
+    }
+  } else {
+    base = a.pupil[j];
+  }
+  float2 mu = a.mu[j];
+  float v = a.v[j], dl = a.delta[j];
+  const float2 d = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, s_bc[0], s_bc[1]);
+  a.mu[j] = mu;
+  a.v[j] = v;
+  a.delta[j] = dl;
+  a.pupil_next[j] = (sidx >= 0) ? csub(base, d) : make_float2(0.f, 0.f);
+}
+
+cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s) {
+  dim3 grid((a.S + 255) / 256, a.Q);
+  pupil_partial_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s) {
+  pupil_update_kernel<<<(a.n * a.n + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Eq. 8 costs in FP64
+__global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int nfid, const double* hp, int nh,
+                                                          double* ring, int* t_dev, double* out3, int advance) {
+  __shared__ double red[8];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nfid; i += 256) s0 += fid[i];
+  for (int i = threadIdx.x; i < nh; i += 256) {
+    s1 += hp[2 * i];
+    s2 += hp[2 * i + 1];
+  }
+  const double a0 = block_sum_double(s0, red);
+  const double a1 = block_sum_double(s1, red);
+  const double a2 = block_sum_double(s2, red);
+  if (threadIdx.x == 0) {
+    if (out3) {
+      out3[0] = a0;
+      out3[1] = a1;
+      out3[2] = a2;
+    }
+    if (ring) {
+      const int t = *t_dev;
+      double* r = ring + 3 * (t % kCostRing);
+      r[0] = a0;
+      r[1] = a1;
+      r[2] = a2;
+    }
+    if (advance) *t_dev += 1;
+  }
+}
+
+cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring, int* t_dev,
+                               double* out3, int advance, cudaStream_t s) {
+  cost_reduce_kernel<<<1, 256, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Eqs. 16-17 (alpha = beta), FP64
+int alpha_blocks(int K, int n) { return K; }
+
+__global__ void __launch_bounds__(256) alpha_partial_kernel(const float* I, int n, int amplitude, double* partial) {
+  __shared__ double red[8];
+  const float* img = I + (size_t)blockIdx.x * n * n;
+  double acc = 0.0;
+  const int m = n - 2;
+  for (int p = threadIdx.x; p < m * m; p += 256) {
+    const int y = p / m + 1, x = p - (p / m) * m + 1;
+    double v[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        double t = (double)img[(y + dy - 1) * n + (x + dx - 1)];
+        if (amplitude) t = sqrt(t > 0.0 ? t : 0.0);
+        v[dy][dx] = t;
+      }
+    // [-1 2 -1; -2 4 -2; -1 2 -1] (Eq. 16)
+    const double r = -v[0][0] + 2.0 * v[0][1] - v[0][2] - 2.0 * v[1][0] + 4.0 * v[1][1] - 2.0 * v[1][2] - v[2][0] +
+                     2.0 * v[2][1] - v[2][2];
+    acc += fabs(r);
+  }
+  const double s = block_sum_double(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void alpha_final_kernel(const double* partial, int K, int n, double* weights, double fa, double fb) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < K; ++i) s += partial[i];
+  const double m = (double)(n - 2) * (double)(n - 2) * (double)K;
+  const double est = 0.2 * sqrt(3.14159265358979323846 / 2.0) * s / m;
+  weights[0] = (fa < 0.0) ? est : fa;
+  weights[1] = (fb < 0.0) ? est : fb;
+}
+
+cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
+                         double fixed_alpha, double fixed_beta, cudaStream_t s) {
+  if (fixed_alpha < 0.0 || fixed_beta < 0.0) {
+    alpha_partial_kernel<<<K, 256, 0, s>>>(I, n, amplitude, partial);
+    alpha_final_kernel<<<1, 32, 0, s>>>(partial, K, n, weights, fixed_alpha, fixed_beta);
+  } else {
+    alpha_final_kernel<<<1, 32, 0, s>>>(partial, 0, n, weights, fixed_alpha, fixed_beta);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ initial state
+__global__ void init_small_kernel(const float* Ic, float2* small, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n * n) return;
+  const int y = j / n, x = j - y * n;
+  const float a = sqrtf(fmaxf(Ic[j], 0.f));
+  small[j] = make_float2(((x + y) & 1) ? -a : a, 0.f);  // (-1)^(x+y): fftshift of the DFT
+}
+
+cudaError_t launch_init_small(const float* I_c, float2* small, int n, cudaStream_t s) {
+  init_small_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(I_c, small, n);
+  return cudaGetLastError();
+}
+
+__global__ void embed_kernel(const float2* small, float2* psi, int n, int N, int oy, int ox, float gain) {
+  const size_t total = (size_t)N * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int y = (int)(i / N), x = (int)(i - (size_t)y * N);
+    const int jy = y - oy, jx = x - ox;
+    float2 v = make_float2(0.f, 0.f);
+    if (jy > 0 && jy < n && jx > 0 && jx < n) v = cscale(small[jy * n + jx], gain);  // Nyquist row/col zeroed
+    psi[i] = v;
+  }
+}
+
+cudaError_t launch_embed(const float2* small, float2* psi, int n, int N, int oy, int ox, float gain, cudaStream_t s) {
+  embed_kernel<<<1024, 256, 0, s>>>(small, psi, n, N, oy, ox, gain);
+  return cudaGetLastError();
+}
+
+__global__ void fill_f2_kernel(float2* p, size_t count, float2 v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+__global__ void fill_f_kernel(float* p, size_t count, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+cudaError_t launch_fill_f2(float2* p, size_t count, float2 value, cudaStream_t s) {
+  fill_f2_kernel<<<1024, 256, 0, s>>>(p, count, value);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_f(float* p, size_t count, float value, cudaStream_t s) {
+  fill_f_kernel<<<1024, 256, 0, s>>>(p, count, value);
+  return cudaGetLastError();
+}
+
+__global__ void support_pupil_kernel(float2* p, const int* sidx_map, int nn) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nn) p[j] = make_float2(sidx_map[j] >= 0 ? 1.f : 0.f, 0.f);
+}
+
+cudaError_t launch_support_pupil(float2* p, const int* sidx_map, int n, cudaStream_t s) {
+  support_pupil_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(p, sidx_map, n * n);
+  return cudaGetLastError();
+}
+
+__global__ void count_nonfinite_kernel(const float* x, size_t count, int* flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) *flag = 1;
+}
+
+cudaError_t launch_count_nonfinite(const float* x, size_t count, int* flag, cudaStream_t s) {
+  count_nonfinite_kernel<<<512, 256, 0, s>>>(x, count, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace elf

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2, FP32 CUDA vs FP64 oracle), derived in the design notes:
+  * forward model, initial state, object, costs: 1e-5 (FP32 FFT rounding ~ 1e-6);
+  * gradients at a developed state: 2e-3 (omega divides residual gradients that
+    cancel to the noise level, amplifying FP32 rounding; Eq. 12);
+  * optimiser state after one iteration from the same developed state: 1e-5
+    (Psi, P); the moments (mu, v, delta) that carry the per-pixel normalised step
+    directly: 2e-3 (v) / 5e-3 (delta);
+  * the full 20-iteration run of workload 0 from the initial state: Psi 2e-3.
+Sizes: tiny (n=16, one gather tile, ragged LED coverage), single LED, n=32,
+the 64/256/49-LED workload, the 128/512/225-LED workload, and the full-size
+256/1024/225-LED workload in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2209_14671_gb300 import build as B
+from paper_2209_14671_gb300 import elfpie as E
+
+from _cases import case, load_state, oracle_state_to_f32, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = ["tiny16", "single_led", "small32", "w0", "w3", "w1"]
+
+TOL_FWD = 1e-5
+TOL_GRAD = 2e-3
+TOL_STATE = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    E.load()
+
+
+def make_elf(c, **opts):
+    return E.Elf(c["n"], c["u"], c["k_xy"], c["na"], c["wl"], c["dx"], options=opts or None)
+
+
+_developed = {}
+
+
+def developed_state(name, iters=3, **opts):
+    """Oracle state after `iters` iterations from its initial state, rounded to FP32."""
+    key = (name, iters, tuple(sorted(opts.items())))
+    if key not in _developed:
+        c = case(name)
+        opt = O.Options(**opts)
+        I = c["I"].astype(np.float64)
+        st = O.init_state(I, c["geo"], c["k_xy"], opt)
+        st, _ = O.run(st, I, c["geo"], opt, iters)
+        _developed[key] = oracle_state_to_f32(st)
+    return _developed[key]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_forward_model_matches_oracle(name):
+    c = case(name)
+    with make_elf(c) as elf:
+        I_gpu = elf.simulate(np.ascontiguousarray(c["obj"].astype(np.complex64)))
+    obj32 = c["obj"].astype(np.complex64).astype(np.complex128)
+    I_ref = O.forward_intensity(O.spectrum_from_object(obj32), c["geo"].support.astype(complex), c["geo"])
+    err = rel(I_gpu, I_ref)
+    print(f"{name} forward rel L2 {err:.2e}")
+    assert err < TOL_FWD
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_initial_state_and_alpha(name):
+    c = case(name)
+    I = c["I"].astype(np.float64)
+    ref = O.init_state(I, c["geo"], c["k_xy"], O.Options())
+    with make_elf(c) as elf:
+        elf.set_measurements(c["I"])
+        st = elf.get_state()
+        obj = elf.get_object()
+        assert st["t"] == 0
+        assert abs(st["alpha"] - ref.alpha) <= 1e-12 * abs(ref.alpha)
+        assert st["beta"] == st["alpha"]
+        e_psi = rel(st["psi"], ref.psi)
+        e_obj = rel(obj, O.object_from_spectrum(ref.psi))
+        print(f"{name} init psi {e_psi:.2e} obj {e_obj:.2e}")
+        assert e_psi < TOL_FWD and e_obj < TOL_FWD
+        assert np.array_equal(elf.get_pupil(), c["geo"].support.astype(np.complex64))
+        assert np.all(st["delta_psi"] == 1.0) and np.all(st["delta_p"] == np.float32(1e-4))
+        assert not np.any(st["mu_psi"]) and not np.any(st["v_psi"])
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_cost_and_gradients_match_oracle(name):
+    c = case(name)
+    st = developed_state(name)
+    I = c["I"].astype(np.float64)
+    opt = O.Options()
+    L_fid, g_fid, g_p, tiles = O.fidelity_cost_grad(st.psi, st.pupil, I, c["geo"], opt, want_tiles=True)
+    L_A, L_P, g_h = O.hessian_cost_grad(st.psi, st.alpha, st.beta, opt)
+    with make_elf(c) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        costs, g_psi, g_pup = elf.cost_grad(st.psi.astype(np.complex64), st.pupil.astype(np.complex64))
+        G = elf.get_tile_grads()
+        sup = elf.get_support()
+    assert np.array_equal(sup, np.flatnonzero(c["geo"].support.ravel()))
+    G_ref = tiles.reshape(tiles.shape[0], -1)[:, sup]
+    e = dict(L_fid=abs(costs[0] - L_fid) / L_fid, L_A=abs(costs[1] - L_A) / L_A, L_P=abs(costs[2] - L_P) / L_P,
+             G=rel(G, G_ref), g_psi=rel(g_psi, g_fid + g_h), g_p=rel(g_pup, g_p))
+    print(name, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["L_fid"] < TOL_FWD and e["L_A"] < TOL_FWD and e["L_P"] < TOL_FWD
+    assert e["G"] < TOL_GRAD and e["g_psi"] < TOL_GRAD and e["g_p"] < TOL_GRAD
+    assert np.all(g_pup.ravel()[~c["geo"].support.ravel()] == 0)
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("learn_pupil", [1, 0])
+def test_one_iteration_from_the_same_state(name, learn_pupil):
+    if name == "w1" and not learn_pupil:
+        pytest.skip("covered by learn_pupil=1 at this size")
+    c = case(name)
+    st = developed_state(name)
+    I = c["I"].astype(np.float64)
+    opt = O.Options(learn_pupil=learn_pupil)
+    ref, costs_ref, _ = O.iteration(st, I, c["geo"], opt)
+    with make_elf(c, learn_pupil=learn_pupil) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        elf.step(1)
+        out = elf.get_state()
+        costs = elf.get_costs()
+    assert out["t"] == st.t + 1 and costs.shape == (st.t + 1, 3)
+    e = {k: rel(out[k], getattr(ref, k)) for k in ("psi", "mu_psi", "v_psi", "delta_psi", "pupil", "mu_p", "v_p",
+                                                  "delta_p")}
+    e["cost"] = float(np.max(np.abs(costs[-1] - np.asarray(costs_ref)) / np.asarray(costs_ref)))
+    print(name, learn_pupil, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["psi"] < TOL_STATE and e["pupil"] < TOL_STATE and e["cost"] < TOL_FWD
+    assert e["mu_psi"] < TOL_GRAD and e["v_psi"] < TOL_GRAD and e["delta_psi"] < 5e-3
+    if learn_pupil:
+        assert e["mu_p"] < TOL_GRAD and e["v_p"] < TOL_GRAD and e["delta_p"] < 5e-3
+
+
+def test_full_run_workload0_matches_oracle():
+    c = case("w0")
+    I = c["I"].astype(np.float64)
+    opt = O.Options()
+    st = O.init_state(I, c["geo"], c["k_xy"], opt)
+    ref, costs_ref = O.run(st, I, c["geo"], opt, c["iters"])
+    with make_elf(c) as elf:
+        elf.set_measurements(c["I"])
+        elf.step(c["iters"])
+        out = elf.get_state()
+        obj = elf.get_object()
+        costs = elf.get_costs()
+    e = dict(psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
+             obj=rel(obj, O.object_from_spectrum(ref.psi)),
+             cost=float(np.max(np.abs(costs - costs_ref) / np.abs(costs_ref))))
+    print("w0 full run", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["psi"] < 2e-3 and e["pupil"] < 2e-3 and e["obj"] < 2e-3 and e["cost"] < 1e-3
+
+
+def test_runs_are_bitwise_reproducible():
+    c = case("w0")
+    outs = []
+    for _ in range(2):
+        with make_elf(c) as elf:
+            elf.set_measurements(c["I"])
+            elf.step(5)
+            outs.append((elf.get_spectrum(), elf.get_pupil(), elf.get_costs()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_state_roundtrip_and_resume():
+    """Checkpoint / resume: 4 iterations == 2 iterations, save, restore into a new handle, 2 more."""
+    c = case("small32")
+    with make_elf(c) as a:
+        a.set_measurements(c["I"])
+        a.step(4)
+        want = a.get_spectrum()
+    with make_elf(c) as b:
+        b.set_measurements(c["I"])
+        b.step(2)
+        ck = b.get_state()
+    with make_elf(c) as d:
+        d.set_measurements(c["I"])
+        d.set_state(ck["psi"], ck["mu_psi"], ck["v_psi"], ck["delta_psi"], ck["pupil"], ck["mu_p"], ck["v_p"],
+                    ck["delta_p"], ck["t"], ck["alpha"], ck["beta"])
+        d.step(2)
+        assert np.array_equal(d.get_spectrum(), want)
+
+
+def test_error_paths_on_gpu():
+    c = case("tiny16")
+    with make_elf(c) as elf:
+        with pytest.raises(E.ElfError) as ei:
+            elf.step(1)
+        assert ei.value.code == E.ELF_ESTATE
+        bad = c["I"].copy()
+        bad[0, 3, 4] = np.nan
+        with pytest.raises(E.ElfError) as ei:
+            elf.set_measurements(bad)
+        assert ei.value.code == E.ELF_EINVAL
+        elf.set_measurements(c["I"])
+        elf.step(0)
+        assert elf.get_costs().shape == (0, 3)
+
+
+def test_device_pointers_through_torch():
+    torch = pytest.importorskip("torch")
+    c = case("small32")
+    dev = torch.device("cuda:0")
+    with make_elf(c) as elf:
+        elf.set_measurements(torch.from_numpy(c["I"]).to(dev))
+        elf.step(3)
+        host = elf.get_spectrum()
+        d = torch.empty((elf.N, elf.N), dtype=torch.complex64, device=dev)
+        elf.get_spectrum(d)
+        assert np.array_equal(d.cpu().numpy(), host)
