@@ -76,6 +76,8 @@ struct elf_handle_s {
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
          *out3 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
+  float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
+  double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
   std::vector<void*> allocs;
 };
 
@@ -192,7 +194,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.v = h->v_p;
   pa.delta = h->delta_p;
   pa.g_out = h->g_p;
-  pa.t_dev = h->t_dev;
+  pa.bc = h->bc;
   pa.N = h->N;
   pa.n = h->n;
   pa.S = h->S;
@@ -227,7 +229,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.v = h->v_psi;
   ga.delta = h->delta_psi;
   ga.g_out = h->g_psi;
-  ga.t_dev = h->t_dev;
+  ga.bc = h->bc;
   ga.N = h->N;
   ga.n = h->n;
   ga.S = h->S;
@@ -251,7 +253,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   }
   ELF_MARK(s0, ELF_STAGE_COST, 0);
   ELF_CK(launch_cost_reduce(h->cost_fid, h->K * h->cs, h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
-                            h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, s0));
+                            h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, h->bc, h->gp,
+                            h->opt.gamma1, h->opt.gamma2, s0));
   ELF_MARK(s0, ELF_STAGE_COST, 1);
   ELF_MARK(s0, ELF_STAGE_ITERATION, 1);
   return ELF_OK;
@@ -284,6 +287,20 @@ int build_graph(elf_handle h) {
     h->graph = nullptr;
     return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
+  return ELF_OK;
+}
+
+// Powers gamma^(t+1) and bias corrections 1/(1 - gamma^(t+1)) of Eq. 19 for the
+// iteration after t.
+int upload_bias(elf_handle h, int t, cudaStream_t s) {
+  static thread_local double gp[2];
+  static thread_local float bc[2];
+  gp[0] = std::pow(h->opt.gamma1, (double)(t + 1));
+  gp[1] = std::pow(h->opt.gamma2, (double)(t + 1));
+  bc[0] = (float)(1.0 / (1.0 - gp[0]));
+  bc[1] = (float)(1.0 / (1.0 - gp[1]));
+  ELF_CK(cudaMemcpyAsync(h->gp, gp, sizeof(gp), cudaMemcpyHostToDevice, s));
+  ELF_CK(cudaMemcpyAsync(h->bc, bc, sizeof(bc), cudaMemcpyHostToDevice, s));
   return ELF_OK;
 }
 
@@ -480,10 +497,12 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->cost_h, (size_t)2 * h->hblocks))) return rc;
   if ((rc = dalloc(h, &h->ring, (size_t)3 * kCostRing))) return rc;
   if ((rc = dalloc(h, &h->weights, 2))) return rc;
-  if ((rc = dalloc(h, &h->alpha_part, (size_t)K))) return rc;
+  if ((rc = dalloc(h, &h->alpha_part, (size_t)alpha_blocks(K, n)))) return rc;
   if ((rc = dalloc(h, &h->out3, 3))) return rc;
   if ((rc = dalloc(h, &h->t_dev, 1))) return rc;
   if ((rc = dalloc(h, &h->flag, 1))) return rc;
+  if ((rc = dalloc(h, &h->bc, 2))) return rc;
+  if ((rc = dalloc(h, &h->gp, 2))) return rc;
   ELF_CK(prepare_tile(n, h->rowsA));
   ELF_CK(prepare_fft(n));
   ELF_CK(prepare_fft(N));
@@ -537,6 +556,7 @@ int elf_set_measurements(elf_handle h, const float* I, int is_device) {
   ELF_CK(launch_fill_f(h->v_p, B, 0.f, s));
   ELF_CK(launch_fill_f(h->delta_p, B, (float)(h->opt.s0_pupil * h->opt.s0_pupil), s));
   ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), s));
+  if (int rc = upload_bias(h, 0, s)) return rc;
   ELF_CK(cudaStreamSynchronize(s));
   h->have_meas = true;
   return ELF_OK;
@@ -646,6 +666,7 @@ int elf_set_state(elf_handle h, const elf_state* st, int is_device) {
   const double w[2] = {st->alpha, st->beta};
   ELF_CK(cudaMemcpyAsync(h->t_dev, &t, sizeof(int), cudaMemcpyHostToDevice, s));
   ELF_CK(cudaMemcpyAsync(h->weights, w, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (int rc = upload_bias(h, t, s)) return rc;
   ELF_CK(cudaStreamSynchronize(s));
   return ELF_OK;
 }

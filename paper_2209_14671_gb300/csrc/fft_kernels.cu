@@ -9,53 +9,66 @@
 
 namespace elf {
 
-constexpr int kFftThreads = 256;
+// Rows (columns) per CTA: few for long transforms so that a 1024 x 1024 pass
+// launches 512 (256) CTAs, more for short ones; one team of TL lanes each.
+template <int L>
+struct FftGrid {
+  static constexpr int TL = FftTeam<L>::TL;
+  static constexpr int RPC = (L >= 512) ? 2 : (L >= 256 ? 4 : 256 / TL);
+  static constexpr int CPC = (L >= 512) ? 4 : (L >= 256 ? 8 : 256 / TL);
+  static constexpr int ROW_THREADS = TL * RPC;
+  static constexpr int COL_THREADS = TL * CPC;
+  static constexpr size_t ROW_SMEM = 8 * ((size_t)L + (size_t)RPC * L);
+  static constexpr size_t COL_SMEM = 8 * ((size_t)L + (size_t)CPC * (L + 1));
+};
 
 template <int L, bool INV>
-__global__ void __launch_bounds__(kFftThreads) fft_rows_kernel(float2* __restrict__ data, const float2* __restrict__ twg) {
-  constexpr int TL = FftTeam<L>::TL;
-  constexpr int NTEAM = kFftThreads / TL;
+__global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(float2* __restrict__ data,
+                                                                             const float2* __restrict__ twg) {
+  using G = FftGrid<L>;
+  constexpr int NT = G::ROW_THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* rows = tw + L;
   const int tid = threadIdx.x;
-  for (int i = tid; i < L; i += kFftThreads) tw[i] = twg[i];
-  const int row0 = blockIdx.x * NTEAM;
-  // coalesced load of NTEAM rows
-  for (int i = tid; i < NTEAM * L; i += kFftThreads) {
+  for (int i = tid; i < L; i += NT) tw[i] = twg[i];
+  const int row0 = blockIdx.x * G::RPC;
+  for (int i = tid; i < G::RPC * L; i += NT) {
     const int r = i / L, x = i - r * L;
     rows[r * L + x] = (row0 + r < L) ? data[(size_t)(row0 + r) * L + x] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int team = tid / TL, lane = tid % TL;
+  const int team = tid / G::TL, lane = tid % G::TL;
   team_fft<L, INV>(rows + team * L, tw, lane, row0 + team < L);
   __syncthreads();
-  for (int i = tid; i < NTEAM * L; i += kFftThreads) {
+  for (int i = tid; i < G::RPC * L; i += NT) {
     const int r = i / L, x = i - r * L;
     if (row0 + r < L) data[(size_t)(row0 + r) * L + x] = rows[r * L + x];
   }
 }
 
 template <int L, bool INV>
-__global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(float2* __restrict__ data, const float2* __restrict__ twg) {
-  constexpr int TL = FftTeam<L>::TL;
-  constexpr int CW = kFftThreads / TL;  // columns per CTA (one team each)
+__global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float2* __restrict__ data,
+                                                                             const float2* __restrict__ twg) {
+  using G = FftGrid<L>;
+  constexpr int NT = G::COL_THREADS;
+  constexpr int CW = G::CPC;
   constexpr int LD = L + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* cols = tw + L;
   const int tid = threadIdx.x;
-  for (int i = tid; i < L; i += kFftThreads) tw[i] = twg[i];
+  for (int i = tid; i < L; i += NT) tw[i] = twg[i];
   const int c0 = blockIdx.x * CW;
-  for (int i = tid; i < CW * L; i += kFftThreads) {
+  for (int i = tid; i < CW * L; i += NT) {
     const int y = i / CW, c = i - y * CW;
     cols[c * LD + y] = (c0 + c < L) ? data[(size_t)y * L + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int team = tid / TL, lane = tid % TL;
+  const int team = tid / G::TL, lane = tid % G::TL;
   team_fft<L, INV>(cols + team * LD, tw, lane, c0 + team < L);
   __syncthreads();
-  for (int i = tid; i < CW * L; i += kFftThreads) {
+  for (int i = tid; i < CW * L; i += NT) {
     const int y = i / CW, c = i - y * CW;
     if (c0 + c < L) data[(size_t)y * L + c0 + c] = cols[c * LD + y];
   }
@@ -63,31 +76,26 @@ __global__ void __launch_bounds__(kFftThreads) fft_cols_kernel(float2* __restric
 
 template <int L, bool INV>
 static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s) {
-  constexpr int TL = FftTeam<L>::TL;
-  constexpr int NTEAM = kFftThreads / TL;
-  const size_t smem_r = 8 * ((size_t)L + (size_t)NTEAM * L);
-  const size_t smem_c = 8 * ((size_t)L + (size_t)NTEAM * (L + 1));
-  const int blocks = (L + NTEAM - 1) / NTEAM;
-  fft_rows_kernel<L, INV><<<blocks, kFftThreads, smem_r, s>>>(data, tw);
-  fft_cols_kernel<L, INV><<<blocks, kFftThreads, smem_c, s>>>(data, tw);
+  using G = FftGrid<L>;
+  fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(data, tw);
+  fft_cols_kernel<L, INV><<<(L + G::CPC - 1) / G::CPC, G::COL_THREADS, G::COL_SMEM, s>>>(data, tw);
   return cudaGetLastError();
 }
 
 template <int L, bool INV>
 static cudaError_t prepare_fft_t() {
-  constexpr int TL = FftTeam<L>::TL;
-  constexpr int NTEAM = kFftThreads / TL;
-  const int smem_r = (int)(8 * ((size_t)L + (size_t)NTEAM * L));
-  const int smem_c = (int)(8 * ((size_t)L + (size_t)NTEAM * (L + 1)));
-  cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_r);
+  using G = FftGrid<L>;
+  cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G::ROW_SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_cols_kernel<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
+  return cudaFuncSetAttribute(fft_cols_kernel<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)G::COL_SMEM);
 }
 
 cudaError_t prepare_fft(int L) {
-#define ELF_PREP_CASE(LL)                                   \
-  case LL: {                                                \
-    cudaError_t e = prepare_fft_t<LL, true>();              \
+#define ELF_PREP_CASE(LL)                                     \
+  case LL: {                                                  \
+    cudaError_t e = prepare_fft_t<LL, true>();                \
     return e != cudaSuccess ? e : prepare_fft_t<LL, false>(); \
   }
   switch (L) {

@@ -64,7 +64,7 @@ struct GatherArgs {
   const float2* gH;       // N x N Hessian gradient (may be null)
   float2* psi; float2* mu; float* v; float* delta;   // state (update mode)
   float2* g_out;          // gradient output (gradient mode)
-  const int* t_dev;
+  const float* bc;        // Eq. 19 bias corrections 1/(1-g1^t), 1/(1-g2^t) of this iteration
   int N, n, S, K, tiles_x, max_list;
   float g1, g2, eta;
   int mode;               // 0 = AdaBelief update, 1 = write g
@@ -80,7 +80,7 @@ struct PupilArgs {
   float2* pupil_next;     // P^{t+1}
   float2* mu; float* v; float* delta;
   float2* g_out;          // gradient mode output (n x n)
-  const int* t_dev;
+  const float* bc;        // Eq. 19 bias corrections of this iteration
   int N, n, S, K, Q, filter;
   float w0, w1;           // 1D Gaussian weights (centre, side), normalised
   float g1, g2, eta;
@@ -92,7 +92,8 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring,
-                               int* t_dev, double* out3, int advance, cudaStream_t s);
+                               int* t_dev, double* out3, int advance, float* bc, double* gp, double g1,
+                               double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
                          double fixed_alpha, double fixed_beta, cudaStream_t s);

@@ -26,15 +26,16 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// Smoothed L1 of a 3-vector (reading A7): cost and omega = h / max(|h|, tau).
+// Smoothed L1 of a 3-vector (reading A7): cost and omega = h / max(|h|, tau)
+// (isotropic), or the same rule per component (anisotropic).
 __device__ __forceinline__ float huber3(float& h0, float& h1, float& h2, float tau, int iso) {
   if (iso) {
-    const float nrm = sqrtf(h0 * h0 + h1 * h1 + h2 * h2);
-    const float den = fmaxf(nrm, tau);
-    h0 /= den;
-    h1 /= den;
-    h2 /= den;
-    return (nrm >= tau) ? nrm : nrm * nrm / (2.f * tau) + 0.5f * tau;
+    const float ss = h0 * h0 + h1 * h1 + h2 * h2;
+    const float inv = rsqrtf(fmaxf(ss, fmaxf(tau * tau, 1e-36f)));
+    h0 *= inv;
+    h1 *= inv;
+    h2 *= inv;
+    return (ss >= tau * tau) ? ss * inv : ss / (2.f * tau) + 0.5f * tau;
   }
   float c = 0.f;
   float* hs[3] = {&h0, &h1, &h2};
@@ -153,14 +154,6 @@ cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ gather + AdaBelief (Eqs. 9, 15, 19)
-__device__ __forceinline__ void bias_corrections(const int* t_dev, float g1, float g2, float* s_bc) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const int t = *t_dev + 1;
-    s_bc[0] = (float)(1.0 / (1.0 - pow((double)g1, (double)t)));
-    s_bc[1] = (float)(1.0 / (1.0 - pow((double)g2, (double)t)));
-  }
-}
-
 // Eq. 19 for one complex parameter; returns the increment Delta.
 __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v, float& delta, float g1, float g2,
                                                  float eta, float bc1, float bc2) {
@@ -176,61 +169,67 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
 
 constexpr int kMaxTileList = 1024;
 
+// One thread per spectrum pixel; a block covers 32 x 8 pixels of one 32 x 32
+// gather tile, whose ascending LED list it stages in shared memory.
 __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
   __shared__ int s_led[kMaxTileList];
   __shared__ int2 s_org[kMaxTileList];
-  __shared__ float s_bc[2];
   extern __shared__ int s_rows[];   // row_xs, row_cnt, row_off (n each)
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int tile = blockIdx.y * a.tiles_x + blockIdx.x;
-  const int l0 = a.tile_ptr[tile], cnt = a.tile_ptr[tile + 1] - l0;
-  for (int i = tid; i < cnt; i += 256) {
-    const int led = a.tile_led[l0 + i];
-    s_led[i] = led;
-    s_org[i] = a.origin[led];
-  }
-  for (int i = tid; i < a.n; i += 256) {
-    s_rows[i] = a.row_xs[i];
-    s_rows[a.n + i] = a.row_cnt[i];
-    s_rows[2 * a.n + i] = a.row_off[i];
-  }
-  if (a.mode == 0) bias_corrections(a.t_dev, a.g1, a.g2, s_bc);
-  __syncthreads();
   const int x = blockIdx.x * kGatherTile + threadIdx.x;
-  for (int r = threadIdx.y; r < kGatherTile; r += 8) {
-    const int y = blockIdx.y * kGatherTile + r;
-    const size_t k = (size_t)y * a.N + x;
-    float2 g = a.gH ? a.gH[k] : make_float2(0.f, 0.f);
-    float2 acc = make_float2(0.f, 0.f);
-    for (int i = 0; i < cnt; ++i) {
-      const int2 o = s_org[i];
-      const int jy = y - o.x, jx = x - o.y;
-      if ((unsigned)jy >= (unsigned)a.n) continue;
-      const int d = jx - s_rows[jy];
-      if ((unsigned)d >= (unsigned)s_rows[a.n + jy]) continue;
-      const float2 p = a.pupil[jy * a.n + jx];
-      const float2 gt = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
-      acc = cadd(acc, cconjmul(p, gt));
-    }
-    g = cadd(g, acc);
-    if (a.mode == 1) {
-      a.g_out[k] = g;
-      continue;
-    }
-    float2 mu = a.mu[k];
-    float v = a.v[k], dl = a.delta[k];
-    const float2 d = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, s_bc[0], s_bc[1]);
-    const float2 p = a.psi[k];
-    a.psi[k] = csub(p, d);
-    a.mu[k] = mu;
-    a.v[k] = v;
-    a.delta[k] = dl;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int tile = (blockIdx.y / (kGatherTile / 8)) * a.tiles_x + blockIdx.x;
+  const int l0 = a.tile_ptr[tile], cnt = a.tile_ptr[tile + 1] - l0;
+  const size_t k = (size_t)y * a.N + x;
+  // state loads first, so that they are in flight during the LED loop
+  float2 g = a.gH ? a.gH[k] : make_float2(0.f, 0.f);
+  float2 mu = make_float2(0.f, 0.f), ps = make_float2(0.f, 0.f);
+  float v = 0.f, dl = 0.f;
+  if (a.mode == 0) {
+    mu = a.mu[k];
+    v = a.v[k];
+    dl = a.delta[k];
+    ps = a.psi[k];
   }
+  if (cnt > 0) {
+    for (int i = tid; i < cnt; i += 256) {
+      const int led = a.tile_led[l0 + i];
+      s_led[i] = led;
+      s_org[i] = a.origin[led];
+    }
+    for (int i = tid; i < a.n; i += 256) {
+      s_rows[i] = a.row_xs[i];
+      s_rows[a.n + i] = a.row_cnt[i];
+      s_rows[2 * a.n + i] = a.row_off[i];
+    }
+  }
+  __syncthreads();
+  float2 acc = make_float2(0.f, 0.f);
+  for (int i = 0; i < cnt; ++i) {
+    const int2 o = s_org[i];
+    const int jy = y - o.x, jx = x - o.y;
+    if ((unsigned)jy >= (unsigned)a.n) continue;
+    const int d = jx - s_rows[jy];
+    if ((unsigned)d >= (unsigned)s_rows[a.n + jy]) continue;
+    const float2 p = a.pupil[jy * a.n + jx];
+    const float2 gt = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
+    acc = cadd(acc, cconjmul(p, gt));
+  }
+  g = cadd(g, acc);
+  if (a.mode == 1) {
+    a.g_out[k] = g;
+    return;
+  }
+  const float2 dlt = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
+  a.psi[k] = csub(ps, dlt);
+  a.mu[k] = mu;
+  a.v[k] = v;
+  a.delta[k] = dl;
 }
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
   if (a.max_list > kMaxTileList) return cudaErrorInvalidValue;
-  dim3 grid(a.tiles_x, a.tiles_x), block(32, 8);
+  dim3 grid(a.tiles_x, a.N / 8), block(32, 8);
   gather_kernel<<<grid, block, 3 * a.n * sizeof(int), s>>>(a);
   return cudaGetLastError();
 }
@@ -261,9 +260,6 @@ __global__ void __launch_bounds__(256) pupil_partial_kernel(const PupilArgs a) {
 }
 
 __global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
-  __shared__ float s_bc[2];
-  if (a.mode == 0) bias_corrections(a.t_dev, a.g1, a.g2, s_bc);
-  __syncthreads();
   const int j = blockIdx.x * 256 + threadIdx.x;
   const int n = a.n;
   if (j >= n * n) return;
@@ -294,7 +290,7 @@ __global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
   }
   float2 mu = a.mu[j];
   float v = a.v[j], dl = a.delta[j];
-  const float2 d = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, s_bc[0], s_bc[1]);
+  const float2 d = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
   a.mu[j] = mu;
   a.v[j] = v;
   a.delta[j] = dl;
@@ -313,8 +309,13 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ Eq. 8 costs in FP64
+// Sums the FP64 partials of Eq. 8's three terms in a fixed order.  When it closes
+// an iteration (advance) it also increments t, advances the running powers
+// gp = (gamma1^(t+1), gamma2^(t+1)) and stores the bias corrections 1/(1 - gp) of
+// Eq. 19 for the next iteration.
 __global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int nfid, const double* hp, int nh,
-                                                          double* ring, int* t_dev, double* out3, int advance) {
+                                                          double* ring, int* t_dev, double* out3, int advance,
+                                                          float* bc, double* gp, double g1, double g2) {
   __shared__ double red[8];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nfid; i += 256) s0 += fid[i];
@@ -338,48 +339,67 @@ __global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int
       r[1] = a1;
       r[2] = a2;
     }
-    if (advance) *t_dev += 1;
+    if (advance) {
+      *t_dev += 1;
+      const double p1 = gp[0] * g1, p2 = gp[1] * g2;
+      gp[0] = p1;
+      gp[1] = p2;
+      bc[0] = (float)(1.0 / (1.0 - p1));
+      bc[1] = (float)(1.0 / (1.0 - p2));
+    }
   }
 }
 
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring, int* t_dev,
-                               double* out3, int advance, cudaStream_t s) {
-  cost_reduce_kernel<<<1, 256, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance);
+                               double* out3, int advance, float* bc, double* gp, double g1, double g2,
+                               cudaStream_t s) {
+  cost_reduce_kernel<<<1, 256, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance, bc, gp, g1, g2);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ Eqs. 16-17 (alpha = beta), FP64
-int alpha_blocks(int K, int n) { return K; }
+// ------------------------------------------------------------------ Eqs. 16-17 (alpha = beta)
+// Per-pixel responses of the 3x3 kernel in FP32, sums of |response| in FP64 in a
+// fixed order: block (image k, 16-row chunk) partials, then one ordered pass.
+constexpr int kAlphaRows = 16;
+
+int alpha_blocks(int K, int n) { return K * ((n - 2 + kAlphaRows - 1) / kAlphaRows); }
 
 __global__ void __launch_bounds__(256) alpha_partial_kernel(const float* I, int n, int amplitude, double* partial) {
   __shared__ double red[8];
-  const float* img = I + (size_t)blockIdx.x * n * n;
-  double acc = 0.0;
+  const int chunks = (n - 2 + kAlphaRows - 1) / kAlphaRows;
+  const int k = blockIdx.x / chunks, ch = blockIdx.x - k * chunks;
+  const float* img = I + (size_t)k * n * n;
   const int m = n - 2;
-  for (int p = threadIdx.x; p < m * m; p += 256) {
-    const int y = p / m + 1, x = p - (p / m) * m + 1;
-    double v[3][3];
+  const int y0 = 1 + ch * kAlphaRows, y1 = min(n - 1, y0 + kAlphaRows);
+  double acc = 0.0;
+  for (int y = y0; y < y1; ++y) {
+    for (int x = 1 + threadIdx.x; x <= m; x += 256) {
+      float v[3][3];
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+      for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        double t = (double)img[(y + dy - 1) * n + (x + dx - 1)];
-        if (amplitude) t = sqrt(t > 0.0 ? t : 0.0);
-        v[dy][dx] = t;
-      }
-    // [-1 2 -1; -2 4 -2; -1 2 -1] (Eq. 16)
-    const double r = -v[0][0] + 2.0 * v[0][1] - v[0][2] - 2.0 * v[1][0] + 4.0 * v[1][1] - 2.0 * v[1][2] - v[2][0] +
-                     2.0 * v[2][1] - v[2][2];
-    acc += fabs(r);
+        for (int dx = 0; dx < 3; ++dx) {
+          float t = img[(y + dy - 1) * n + (x + dx - 1)];
+          if (amplitude) t = sqrtf(fmaxf(t, 0.f));
+          v[dy][dx] = t;
+        }
+      // [-1 2 -1; -2 4 -2; -1 2 -1] (Eq. 16)
+      const float r = (2.f * v[0][1] - v[0][0] - v[0][2]) + 2.f * (2.f * v[1][1] - v[1][0] - v[1][2]) +
+                      (2.f * v[2][1] - v[2][0] - v[2][2]);
+      acc += (double)fabsf(r);
+    }
   }
   const double s = block_sum_double(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void alpha_final_kernel(const double* partial, int K, int n, double* weights, double fa, double fb) {
+__global__ void __launch_bounds__(256) alpha_final_kernel(const double* partial, int nparts, int K, int n,
+                                                          double* weights, double fa, double fb) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) acc += partial[i];
+  const double s = block_sum_double(acc, red);
   if (threadIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < K; ++i) s += partial[i];
   const double m = (double)(n - 2) * (double)(n - 2) * (double)K;
   const double est = 0.2 * sqrt(3.14159265358979323846 / 2.0) * s / m;
   weights[0] = (fa < 0.0) ? est : fa;
@@ -389,10 +409,11 @@ __global__ void alpha_final_kernel(const double* partial, int K, int n, double* 
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
                          double fixed_alpha, double fixed_beta, cudaStream_t s) {
   if (fixed_alpha < 0.0 || fixed_beta < 0.0) {
-    alpha_partial_kernel<<<K, 256, 0, s>>>(I, n, amplitude, partial);
-    alpha_final_kernel<<<1, 32, 0, s>>>(partial, K, n, weights, fixed_alpha, fixed_beta);
+    const int nb = alpha_blocks(K, n);
+    alpha_partial_kernel<<<nb, 256, 0, s>>>(I, n, amplitude, partial);
+    alpha_final_kernel<<<1, 256, 0, s>>>(partial, nb, K, n, weights, fixed_alpha, fixed_beta);
   } else {
-    alpha_final_kernel<<<1, 32, 0, s>>>(partial, 0, n, weights, fixed_alpha, fixed_beta);
+    alpha_final_kernel<<<1, 256, 0, s>>>(partial, 0, K, n, weights, fixed_alpha, fixed_beta);
   }
   return cudaGetLastError();
 }
@@ -455,14 +476,20 @@ cudaError_t launch_support_pupil(float2* p, const int* sidx_map, int n, cudaStre
 
 __global__ void count_nonfinite_kernel(const float* x, size_t count, int* flag) {
   int bad = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+  const size_t n4 = count / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x);  // cudaMalloc'd: 16-byte aligned
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = x4[i];
+    bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+  }
+  for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
     bad |= !isfinite(x[i]);
   bad = __syncthreads_or(bad);
   if (bad && threadIdx.x == 0) *flag = 1;
 }
 
 cudaError_t launch_count_nonfinite(const float* x, size_t count, int* flag, cudaStream_t s) {
-  count_nonfinite_kernel<<<512, 256, 0, s>>>(x, count, flag);
+  count_nonfinite_kernel<<<4 * 152, 256, 0, s>>>(x, count, flag);
   return cudaGetLastError();
 }
 
