@@ -172,6 +172,27 @@ int elf_get_stage_times(elf_handle h, float* ms, int max_stages);
 /* Number of kernel launches in one iteration (kernel nodes of the iteration graph). */
 int elf_graph_kernel_count(elf_handle h);
 
+/* ---- No-allocation entry point (the paper has no counterpart to this call) ----
+ * Some callers cannot allocate device memory: a process whose device memory
+ * belongs to another allocator or to a fixed budget, or code that runs while its
+ * framework forbids new allocations.  For them this computes the alpha = beta
+ * weight of Eq. 16 (fidelity 0) or Eq. 17 (fidelity 1) without a handle and
+ * without allocating: no cudaMalloc, cudaFree or allocating library routine.
+ * I: device [n_led][n_lowres][n_lowres] float (3 <= n_lowres <= 4096);
+ * weights: device, 2 doubles (alpha, beta), written in stream order on
+ * cuda_stream (a cudaStream_t, may be NULL); the call does not synchronise.
+ * Scratch: a static device array of ELF_NOALLOC_WEIGHT_MAX_PARTIALS doubles
+ * (128 KB) that every GPU loading this library holds until the process exits.
+ * A problem needing more partials than that (n_led * ceil((n_lowres - 2) / 16))
+ * is rejected with ELF_EINVAL before any GPU work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls share
+ * the array; each call overwrites every partial it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU race. */
+#define ELF_NOALLOC_WEIGHT_MAX_PARTIALS 16384
+int elf_estimate_weights_noalloc(const float* I, int n_led, int n_lowres, int fidelity, double* weights,
+                                 void* cuda_stream);
+
 void elf_destroy(elf_handle h);
 const char* elf_strerror(int code);
 const char* elf_last_error(void);

@@ -43,6 +43,11 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
+namespace elf {
+// error reporting for the entry points defined in other translation units
+int noalloc_set_error(int code, const char* msg) { return set_error(code, msg); }
+}  // namespace elf
+
 struct elf_handle_s {
   int n = 0, u = 0, N = 0, K = 0, S = 0, Blo = 0, nb = 0, rowsA = 0, cs = 1, Q = 1;
   int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;

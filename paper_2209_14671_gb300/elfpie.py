@@ -61,6 +61,7 @@ SIGNATURES = {
     "elf_set_tracing": (c_int, [c_void_p, c_int]),
     "elf_get_stage_times": (c_int, [c_void_p, P_float, c_int]),
     "elf_graph_kernel_count": (c_int, [c_void_p]),
+    "elf_estimate_weights_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "elf_destroy": (None, [c_void_p]),
     "elf_strerror": (ctypes.c_char_p, [c_int]),
     "elf_last_error": (ctypes.c_char_p, []),
@@ -280,6 +281,18 @@ class Elf:
         pi, dev2 = _ptr(out)
         _check(load().elf_simulate(self._h, c_void_p(po), c_void_p(pi), dev2), "elf_simulate")
         return out
+
+
+def estimate_weights_noalloc(I_dev, n_led: int, n_lowres: int, fidelity: int, weights_dev, stream=None):
+    """Eq. 16/17 alpha = beta into ``weights_dev`` (device, 2 float64) without any device
+    allocation, for callers that cannot allocate; asynchronous on ``stream``."""
+    pi, dev_i = _ptr(I_dev)
+    pw, dev_w = _ptr(weights_dev)
+    if not (dev_i and dev_w):
+        raise ValueError("I and weights must be device tensors")
+    _check(load().elf_estimate_weights_noalloc(c_void_p(pi), int(n_led), int(n_lowres), int(fidelity),
+                                               c_void_p(pw), c_void_p(_stream_handle(stream))),
+           "elf_estimate_weights_noalloc")
 
 
 def exported_symbols_from_header(header_path: str) -> list[str]:
