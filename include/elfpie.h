@@ -172,6 +172,35 @@ int elf_get_stage_times(elf_handle h, float* ms, int max_stages);
 /* Number of kernel launches in one iteration (kernel nodes of the iteration graph). */
 int elf_graph_kernel_count(elf_handle h);
 
+/* ---- Serving: continuous batching of independent reconstructions ----------
+ * (Not in the paper.)  A server admits queued requests in arrival order while a
+ * device-memory budget and a slot count allow, runs every admitted request's
+ * whole job (measurements upload, initial state, n_iter iterations, object) on
+ * its own stream so that jobs overlap on the device, and retires finished jobs
+ * without blocking.  Handles are pooled per (problem, options) and reused; idle
+ * pooled handles are freed, least recently used first, when a new shape needs
+ * room.  A request's result is bitwise the same as a lone run of the same job. */
+typedef struct elf_server_s* elf_server;
+/* budget_bytes: device memory the server may hold; max_active: concurrent jobs. */
+int elf_server_create(size_t budget_bytes, int max_active, elf_server* out);
+/* Queues a request.  I [K][n][n] float (host; pinned memory makes the upload
+ * asynchronous) is NOT copied: it must stay valid and unchanged until the
+ * request's result has been collected.  tag identifies the request (unique among
+ * unfinished and uncollected ones).  A problem that cannot fit the budget even
+ * alone -> ELF_ENOMEM.  Non-finite inputs are not checked here. */
+int elf_server_submit(elf_server s, const elf_problem* prob, const elf_options* opt, const float* I, int n_iter,
+                      long long tag);
+/* Non-blocking: retires finished jobs (their tags go to done_tags, at most
+ * max_done of them, count in *n_done), then admits queued requests that fit. */
+int elf_server_progress(elf_server s, long long* done_tags, int max_done, int* n_done);
+/* Copies a finished request's object O [N][N][2] float to host memory and
+ * forgets the request.  ELF_ESTATE if it has not finished. */
+int elf_server_result(elf_server s, long long tag, float* obj);
+/* Device bytes held, jobs in flight, requests waiting, handles created so far. */
+int elf_server_stats(elf_server s, size_t* used_bytes, int* n_active, int* n_queued, int* n_created);
+/* Waits for jobs in flight, then frees everything. */
+void elf_server_destroy(elf_server s);
+
 /* ---- No-allocation entry point (the paper has no counterpart to this call) ----
  * Some callers cannot allocate device memory: a process whose device memory
  * belongs to another allocator or to a fixed budget, or code that runs while its

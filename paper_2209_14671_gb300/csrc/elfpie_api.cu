@@ -81,6 +81,7 @@ struct elf_handle_s {
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
          *out3 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
+  size_t device_bytes = 0;  // sum of this handle's device allocations
   float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
   double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
   std::vector<void*> allocs;
@@ -96,6 +97,7 @@ int dalloc(elf_handle h, T** p, size_t count) {
     return set_error(e == cudaErrorMemoryAllocation ? ELF_ENOMEM : ELF_ECUDA,
                      std::string("cudaMalloc: ") + cudaGetErrorString(e));
   h->allocs.push_back(v);
+  h->device_bytes += count * sizeof(T) > 0 ? count * sizeof(T) : 16;
   *p = static_cast<T*>(v);
   return ELF_OK;
 }
@@ -108,13 +110,17 @@ int upload(elf_handle h, T** p, const std::vector<T>& v) {
   return ELF_OK;
 }
 
+// Team twiddles of a length-L transform (fft.cuh): tw[k1 * Q + l] = e^{-2 pi i l k1 / L},
+// computed in FP64.
 std::vector<float2> twiddles(int L) {
+  const int Q = fft_team_lanes(L), P = L / Q;
   std::vector<float2> t(L);
   const double pi = 3.14159265358979323846;
-  for (int k = 0; k < L; ++k) {
-    const double a = -2.0 * pi * (double)k / (double)L;
-    t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+  for (int k1 = 0; k1 < P; ++k1)
+    for (int l = 0; l < Q; ++l) {
+      const double a = -2.0 * pi * (double)((long)l * k1 % L) / (double)L;
+      t[k1 * Q + l] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
   return t;
 }
 
@@ -286,7 +292,8 @@ int build_graph(elf_handle h) {
         if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
       }
   }
-  e = cudaGraphInstantiate(&h->graph, g, 0);
+  // per-node priorities: the Hessian branch was captured from the high-priority stream
+  e = cudaGraphInstantiateWithFlags(&h->graph, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     h->graph = nullptr;
@@ -459,7 +466,11 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   // streams and events
   h->user = static_cast<cudaStream_t>(stream);
   ELF_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-  ELF_CK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+  // the Hessian branch gets the highest priority so that its short kernels are
+  // scheduled ahead of the queued tile-kernel CTAs instead of after them
+  int prio_low = 0, prio_high = 0;
+  ELF_CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  ELF_CK(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_high));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));
@@ -531,22 +542,15 @@ int elf_create(const elf_problem* p, const elf_options* o, void* stream, elf_han
   return ELF_OK;
 }
 
-int elf_set_measurements(elf_handle h, const float* I, int is_device) {
-  if (int rc = check(h)) return rc;
-  if (!I) return set_error(ELF_EINVAL, "null measurements");
-  (void)is_device;
+}  // extern "C"
+
+namespace elf {
+
+// Initial state of elf_set_measurements from the measurements already in h->I,
+// enqueued on the handle's stream without synchronising.
+int init_state_async(elf_handle h) {
   const size_t B = (size_t)h->n * h->n, A = (size_t)h->N * h->N;
   cudaStream_t s = h->user;
-  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * B * sizeof(float), cudaMemcpyDefault, s));
-  ELF_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-  ELF_CK(launch_count_nonfinite(h->I, (size_t)h->K * B, h->flag, s));
-  int bad = 0;
-  ELF_CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  ELF_CK(cudaStreamSynchronize(s));
-  if (bad) {
-    h->have_meas = false;
-    return set_error(ELF_EINVAL, "measurements contain NaN or Inf");
-  }
   // alpha = beta (Eqs. 16-17) and the initial state (reading A9)
   ELF_CK(launch_alpha(h->I, h->K, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
   ELF_CK(launch_init_small(h->I + (size_t)h->centre * B, h->small, h->n, s));
@@ -561,11 +565,60 @@ int elf_set_measurements(elf_handle h, const float* I, int is_device) {
   ELF_CK(launch_fill_f(h->v_p, B, 0.f, s));
   ELF_CK(launch_fill_f(h->delta_p, B, (float)(h->opt.s0_pupil * h->opt.s0_pupil), s));
   ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), s));
-  if (int rc = upload_bias(h, 0, s)) return rc;
-  ELF_CK(cudaStreamSynchronize(s));
+  ELF_CK(launch_init_bias(h->bc, h->gp, h->opt.gamma1, h->opt.gamma2, s));
   h->have_meas = true;
   return ELF_OK;
 }
+
+// Asynchronous job pieces for the serving scheduler (server.cu).
+int handle_set_measurements_async(elf_handle h, const float* I) {
+  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * h->n * h->n * sizeof(float), cudaMemcpyDefault, h->user));
+  return init_state_async(h);
+}
+
+int handle_get_object_async(elf_handle h, float* obj) {
+  const size_t A = (size_t)h->N * h->N;
+  ELF_CK(cudaMemcpyAsync(h->ot, h->psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->user));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user));
+  ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
+  ELF_CK(cudaMemcpyAsync(obj, h->ot, A * sizeof(float2), cudaMemcpyDefault, h->user));
+  return ELF_OK;
+}
+
+size_t handle_device_bytes(elf_handle h) { return h->device_bytes; }
+cudaStream_t handle_stream(elf_handle h) { return h->user; }
+int handle_sizes(elf_handle h, int* n, int* N, int* K) {
+  *n = h->n;
+  *N = h->N;
+  *K = h->K;
+  return ELF_OK;
+}
+int handle_set_error(int code, const char* msg) { return set_error(code, msg); }
+
+}  // namespace elf
+
+extern "C" int elf_set_measurements(elf_handle h, const float* I, int is_device) {
+  if (int rc = check(h)) return rc;
+  if (!I) return set_error(ELF_EINVAL, "null measurements");
+  (void)is_device;
+  const size_t B = (size_t)h->n * h->n;
+  cudaStream_t s = h->user;
+  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * B * sizeof(float), cudaMemcpyDefault, s));
+  ELF_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+  ELF_CK(launch_count_nonfinite(h->I, (size_t)h->K * B, h->flag, s));
+  int bad = 0;
+  ELF_CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ELF_CK(cudaStreamSynchronize(s));
+  if (bad) {
+    h->have_meas = false;
+    return set_error(ELF_EINVAL, "measurements contain NaN or Inf");
+  }
+  if (int rc = init_state_async(h)) return rc;
+  ELF_CK(cudaStreamSynchronize(s));
+  return ELF_OK;
+}
+
+extern "C" {
 
 int elf_step(elf_handle h, int n_iter) {
   if (int rc = check(h)) return rc;

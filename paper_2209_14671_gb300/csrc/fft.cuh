@@ -1,12 +1,18 @@
-// Device building blocks: complex arithmetic and a shared-memory Stockham FFT.
+// Device building blocks: complex arithmetic and a shared-memory FFT.
 //
-// A length-L transform is owned by a "team" of TL = min(32, L/8) lanes of one
-// warp, so all of its synchronisation is __syncwarp().  Each pass reads the whole
-// vector into registers (radix-R butterflies, R = 8 while possible, then 4 or 2),
-// synchronises, and writes it back in Stockham (self-sorting) order, so the
-// output is in natural order with no bit reversal.  Transforms are unnormalised:
-// forward X[k] = sum_x x[x] e^{-2 pi i k x / L}, inverse with e^{+2 pi i k x / L}.
-// Twiddles W_L^k = e^{-2 pi i k / L} come from a table built in FP64 on the host.
+// A length-L transform, L = P * Q (P >= Q, powers of two), is owned by a team of
+// Q lanes of one warp and done in two passes over its shared-memory buffer
+// (the "four-step" split of the DFT index):
+//   pass 1  lane l reads x[l + Q j] (j < P), does a P-point DFT in registers,
+//           multiplies by W_L^{l k1} and writes the result transposed (k1-major);
+//   pass 2  lane l takes rows k1 = l + Q m, does Q-point DFTs in registers and
+//           writes X[k1 + P k2] in natural order.
+// Buffers use the padded index p(i) = i + floor(i / Q) (one spare element after
+// every Q), which makes the strided accesses of both passes bank-conflict free
+// within each half-warp.  Twiddles W_L^{l k1} come from a table laid out
+// [k1][l] (built in FP64 on the host), the constants of the in-register DFTs
+// are exact values of cos(k pi / 16).  Transforms are unnormalised: forward
+// X[k] = sum_x x[x] e^{-2 pi i k x / L}, inverse with e^{+2 pi i k x / L}.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,136 +31,179 @@ __device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// cos(k pi / 16), k = 0..8
+__device__ __forceinline__ constexpr float cos16(int k) {
+  return k == 0 ? 1.0f
+       : k == 1 ? 0.98078528040323043058f
+       : k == 2 ? 0.92387953251128673848f
+       : k == 3 ? 0.83146961230254523567f
+       : k == 4 ? 0.70710678118654757274f
+       : k == 5 ? 0.55557023301960228867f
+       : k == 6 ? 0.38268343236508983729f
+       : k == 7 ? 0.19509032201612833135f
+                : 0.0f;
+}
+
+// W_32^m = e^{-+2 pi i m / 32} for 0 <= m < 16 (sign by direction)
+template <bool INV>
+__device__ __forceinline__ float2 w32(int m) {
+  const float c = (m <= 8) ? cos16(m) : -cos16(16 - m);
+  const float s = (m <= 8) ? cos16(8 - m) : cos16(m - 8);  // sin(m pi / 16)
+  return INV ? make_float2(c, s) : make_float2(c, -s);
+}
+
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_rot(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dft_small(float2* v);
-
-template <>
-__device__ __forceinline__ void dft_small<2, false>(float2* v) {
-  float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-template <>
-__device__ __forceinline__ void dft_small<2, true>(float2* v) {
-  float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-
+// o * W_32^m with the trivial factors (m = 0: 1, m = 8: -+i) resolved at compile time
 template <bool INV>
-__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-  // X[k] = sum_n x[n] (-+i)^{nk}
-  float2 c0 = cadd(x0, x2), c1 = csub(x0, x2);
-  float2 c2 = cadd(x1, x3), c3 = mul_rot<INV>(csub(x1, x3));
-  x0 = cadd(c0, c2);
-  x2 = csub(c0, c2);
-  x1 = cadd(c1, c3);
-  x3 = csub(c1, c3);
+__device__ __forceinline__ float2 twmul(float2 o, int m) {
+  if (m == 0) return o;
+  if (m == 8) return mul_rot<INV>(o);
+  return cmul(o, w32<INV>(m));
 }
 
-template <>
-__device__ __forceinline__ void dft_small<4, false>(float2* v) { dft4<false>(v[0], v[1], v[2], v[3]); }
-template <>
-__device__ __forceinline__ void dft_small<4, true>(float2* v) { dft4<true>(v[0], v[1], v[2], v[3]); }
-
-template <bool INV>
-__device__ __forceinline__ void dft8(float2* v) {
-  // radix-2 split: even outputs from a[n] + a[n+4], odd outputs from
-  // (a[n] - a[n+4]) W8^n, each through a 4-point DFT.
-  const float h = 0.70710678118654752440f;  // 1/sqrt(2)
-  float2 b0 = cadd(v[0], v[4]), b4 = csub(v[0], v[4]);
-  float2 b1 = cadd(v[1], v[5]), b5 = csub(v[1], v[5]);
-  float2 b2 = cadd(v[2], v[6]), b6 = csub(v[2], v[6]);
-  float2 b3 = cadd(v[3], v[7]), b7 = csub(v[3], v[7]);
-  // W8^1 = (1 -+ i)/sqrt2, W8^2 = -+i, W8^3 = (-1 -+ i)/sqrt2
-  if (INV) {
-    b5 = make_float2((b5.x - b5.y) * h, (b5.x + b5.y) * h);
-    b6 = make_float2(-b6.y, b6.x);
-    b7 = make_float2((-b7.x - b7.y) * h, (b7.x - b7.y) * h);
-  } else {
-    b5 = make_float2((b5.x + b5.y) * h, (b5.y - b5.x) * h);
-    b6 = make_float2(b6.y, -b6.x);
-    b7 = make_float2((b7.y - b7.x) * h, (-b7.x - b7.y) * h);
+// In-register DFT of M values (natural order in and out), radix-2 recursion
+// with hand-written 2, 4 and 8-point kernels.
+template <int M, bool INV>
+struct Dft {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 e[M / 2], o[M / 2];
+#pragma unroll
+    for (int k = 0; k < M / 2; ++k) {
+      e[k] = v[2 * k];
+      o[k] = v[2 * k + 1];
+    }
+    Dft<M / 2, INV>::run(e);
+    Dft<M / 2, INV>::run(o);
+#pragma unroll
+    for (int k = 0; k < M / 2; ++k) {
+      const float2 t = twmul<INV>(o[k], k * (32 / M));
+      v[k] = cadd(e[k], t);
+      v[k + M / 2] = csub(e[k], t);
+    }
   }
-  dft4<INV>(b0, b1, b2, b3);
-  dft4<INV>(b4, b5, b6, b7);
-  v[0] = b0; v[2] = b1; v[4] = b2; v[6] = b3;
-  v[1] = b4; v[3] = b5; v[5] = b6; v[7] = b7;
-}
+};
 
-template <>
-__device__ __forceinline__ void dft_small<8, false>(float2* v) { dft8<false>(v); }
-template <>
-__device__ __forceinline__ void dft_small<8, true>(float2* v) { dft8<true>(v); }
+template <bool INV>
+struct Dft<1, INV> {
+  static __device__ __forceinline__ void run(float2*) {}
+};
+
+template <bool INV>
+struct Dft<2, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 c0 = cadd(v[0], v[2]), c1 = csub(v[0], v[2]);
+    const float2 c2 = cadd(v[1], v[3]), c3 = mul_rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(c0, c2);
+    v[2] = csub(c0, c2);
+    v[1] = cadd(c1, c3);
+    v[3] = csub(c1, c3);
+  }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    // even outputs from a[n] + a[n+4], odd outputs from (a[n] - a[n+4]) W8^n
+    const float h = cos16(4);
+    float2 b[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      b[k] = cadd(v[k], v[k + 4]);
+      b[k + 4] = csub(v[k], v[k + 4]);
+    }
+    if (INV) {
+      b[5] = make_float2((b[5].x - b[5].y) * h, (b[5].x + b[5].y) * h);
+      b[6] = make_float2(-b[6].y, b[6].x);
+      b[7] = make_float2((-b[7].x - b[7].y) * h, (b[7].x - b[7].y) * h);
+    } else {
+      b[5] = make_float2((b[5].x + b[5].y) * h, (b[5].y - b[5].x) * h);
+      b[6] = make_float2(b[6].y, -b[6].x);
+      b[7] = make_float2((b[7].y - b[7].x) * h, (-b[7].x - b[7].y) * h);
+    }
+    Dft<4, INV>::run(b);
+    Dft<4, INV>::run(b + 4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = b[k];
+      v[2 * k + 1] = b[k + 4];
+    }
+  }
+};
 
 template <int L>
 struct FftTeam {
-  static constexpr int TL = (L / 8 < 32) ? (L / 8) : 32;  // lanes per transform
-  static constexpr int PER_WARP = 32 / TL;                 // transforms per warp
-  static_assert(L >= 16 && (L & (L - 1)) == 0, "power-of-two length >= 16");
+  static_assert(L >= 16 && L <= 1024 && (L & (L - 1)) == 0, "power-of-two length 16..1024");
+  static constexpr int LOG = (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7 : (L == 256) ? 8
+                           : (L == 512) ? 9 : 10;
+  static constexpr int Q = 1 << (LOG / 2);        // lanes per transform
+  static constexpr int P = L / Q;                 // values per lane (P >= Q)
+  static constexpr int TL = Q;
+  static constexpr int PER_WARP = 32 / Q;
+  static constexpr int PADDED = L + L / Q;        // buffer length with padding
+  static __device__ __forceinline__ int pidx(int i) { return i + (i >> (LOG / 2)); }
 };
 
-// One Stockham pass with radix R after NS points have been combined.
-template <int L, int R, int NS, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* buf, const float2* __restrict__ tw, int lane, bool active) {
-  constexpr int TL = FftTeam<L>::TL;
-  constexpr int NB = L / R;
-  constexpr int PER = NB / TL;
-  static_assert(PER >= 1 && NB % TL == 0, "team too large for this pass");
-  float2 v[PER][R];
-  if (active) {
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-      const int j = lane + m * TL;
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[m][r] = buf[j + r * NB];
-      if (NS > 1) {
-        const int jm = j & (NS - 1);
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[(jm * r) * (L / (NS * R))];
-          if (INV) w.y = -w.y;
-          v[m][r] = cmul(v[m][r], w);
-        }
-      }
-      dft_small<R, INV>(v[m]);
-    }
-  }
-  __syncwarp();
-  if (active) {
-#pragma unroll
-    for (int m = 0; m < PER; ++m) {
-      const int j = lane + m * TL;
-      const int jm = j & (NS - 1);
-      const int base = (j - jm) * R + jm;
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[base + r * NS] = v[m][r];
-    }
-  }
-  __syncwarp();
-}
-
-template <int L, int NS, bool INV>
-__device__ __forceinline__ void fft_passes(float2* buf, const float2* __restrict__ tw, int lane, bool active) {
-  if constexpr (NS < L) {
-    constexpr int REM = L / NS;
-    constexpr int R = (REM >= 8) ? 8 : REM;
-    stockham_pass<L, R, NS, INV>(buf, tw, lane, active);
-    fft_passes<L, NS * R, INV>(buf, tw, lane, active);
-  }
-}
-
-// In-place length-L transform of buf[0..L) in shared memory by one team.
-// Every lane of the warp must call this (inactive lanes pass active = false).
+// Twiddle table of a team transform: tw[k1 * Q + l] = W_L^{l k1} (forward sign).
+// In-place transform of buf (padded layout) by one team.  Inputs outside
+// [lo, lo + cnt) are taken as zero without being read.  Every lane of the warp
+// must call this (inactive lanes pass active = false).
 template <int L, bool INV>
-__device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__ tw, int lane, bool active) {
-  fft_passes<L, 1, INV>(buf, tw, lane, active);
+__device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__ tw, int lane, bool active,
+                                         int lo = 0, int cnt = L) {
+  using T = FftTeam<L>;
+  constexpr int P = T::P, Q = T::Q;
+  float2 v[P];
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      v[j] = ((unsigned)(lane + Q * j - lo) < (unsigned)cnt) ? buf[lane + (Q + 1) * j] : make_float2(0.f, 0.f);
+    Dft<P, INV>::run(v);
+#pragma unroll
+    for (int k = 1; k < P; ++k) {
+      float2 w = tw[k * Q + lane];
+      if (INV) w.y = -w.y;
+      v[k] = cmul(v[k], w);
+    }
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) buf[k * (Q + 1) + lane] = v[k];
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P / Q; ++m) {
+      const int k1 = lane + Q * m;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) v[m * Q + l] = buf[k1 * (Q + 1) + l];
+      Dft<Q, INV>::run(v + m * Q);
+    }
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P / Q; ++m) {
+      const int k1 = lane + Q * m;
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) buf[T::pidx(k1 + P * k2)] = v[m * Q + k2];
+    }
+  }
+  __syncwarp();
 }
 
 }  // namespace elf

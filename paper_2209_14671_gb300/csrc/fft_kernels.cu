@@ -14,36 +14,66 @@ namespace elf {
 template <int L>
 struct FftGrid {
   static constexpr int TL = FftTeam<L>::TL;
-  static constexpr int RPC = (L >= 512) ? 2 : (L >= 256 ? 4 : 256 / TL);
-  static constexpr int CPC = (L >= 512) ? 4 : (L >= 256 ? 8 : 256 / TL);
+  static constexpr int PL = FftTeam<L>::PADDED;
+  static constexpr int RPC = (128 / TL < L) ? 128 / TL : L;  // rows per CTA (one team each)
+  static constexpr int CPC = (128 / TL < L) ? 128 / TL : L;  // columns per CTA
   static constexpr int ROW_THREADS = TL * RPC;
   static constexpr int COL_THREADS = TL * CPC;
-  static constexpr size_t ROW_SMEM = 8 * ((size_t)L + (size_t)RPC * L);
-  static constexpr size_t COL_SMEM = 8 * ((size_t)L + (size_t)CPC * (L + 1));
+  static constexpr int LD = PL + 1;               // column pitch (odd)
+  static constexpr size_t ROW_SMEM = 8 * ((size_t)L + (size_t)RPC * PL);
+  static_assert(L % CPC == 0 && L % RPC == 0, "rows and columns per CTA divide L");
+  static constexpr size_t COL_SMEM = 8 * ((size_t)L + (size_t)CPC * LD);
 };
 
+// Rows pass: each team transforms one row, reading its pass-1 inputs straight
+// from global memory into registers (coalesced across lanes, all loads in
+// flight at once) and writing its pass-2 outputs straight back; shared memory
+// only carries the transpose between the two passes.
 template <int L, bool INV>
 __global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(float2* __restrict__ data,
                                                                              const float2* __restrict__ twg) {
   using G = FftGrid<L>;
+  using T = FftTeam<L>;
   constexpr int NT = G::ROW_THREADS;
+  constexpr int P = T::P, Q = T::Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* rows = tw + L;
   const int tid = threadIdx.x;
-  for (int i = tid; i < L; i += NT) tw[i] = twg[i];
-  const int row0 = blockIdx.x * G::RPC;
-  for (int i = tid; i < G::RPC * L; i += NT) {
-    const int r = i / L, x = i - r * L;
-    rows[r * L + x] = (row0 + r < L) ? data[(size_t)(row0 + r) * L + x] : make_float2(0.f, 0.f);
+  const int team = tid / Q, lane = tid % Q;
+  const int row = blockIdx.x * G::RPC + team;
+  const bool act = row < L;
+  float2* g = data + (size_t)(act ? row : 0) * L;
+  float2 v[P];
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) v[j] = g[lane + Q * j];
   }
+  for (int i = tid; i < L; i += NT) tw[i] = twg[i];
   __syncthreads();
-  const int team = tid / G::TL, lane = tid % G::TL;
-  team_fft<L, INV>(rows + team * L, tw, lane, row0 + team < L);
-  __syncthreads();
-  for (int i = tid; i < G::RPC * L; i += NT) {
-    const int r = i / L, x = i - r * L;
-    if (row0 + r < L) data[(size_t)(row0 + r) * L + x] = rows[r * L + x];
+  float2* buf = rows + team * G::PL;
+  if (act) {
+    Dft<P, INV>::run(v);
+#pragma unroll
+    for (int k = 1; k < P; ++k) {
+      float2 w = tw[k * Q + lane];
+      if (INV) w.y = -w.y;
+      v[k] = cmul(v[k], w);
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) buf[k * (Q + 1) + lane] = v[k];
+  }
+  __syncwarp();
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < P / Q; ++m) {
+      const int k1 = lane + Q * m;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) v[m * Q + l] = buf[k1 * (Q + 1) + l];
+      Dft<Q, INV>::run(v + m * Q);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) g[k1 + P * k2] = v[m * Q + k2];
+    }
   }
 }
 
@@ -53,24 +83,30 @@ __global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float
   using G = FftGrid<L>;
   constexpr int NT = G::COL_THREADS;
   constexpr int CW = G::CPC;
-  constexpr int LD = L + 1;
+  constexpr int LD = G::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* cols = tw + L;
   const int tid = threadIdx.x;
   for (int i = tid; i < L; i += NT) tw[i] = twg[i];
   const int c0 = blockIdx.x * CW;
+  // asynchronous 8-byte copies, all in flight at once (CW divides L, so c0 + c < L)
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(cols);
   for (int i = tid; i < CW * L; i += NT) {
     const int y = i / CW, c = i - y * CW;
-    cols[c * LD + y] = (c0 + c < L) ? data[(size_t)y * L + c0 + c] : make_float2(0.f, 0.f);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sbase + 8u * (c * LD + FftTeam<L>::pidx(y))),
+                 "l"(data + (size_t)y * L + c0 + c)
+                 : "memory");
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int team = tid / G::TL, lane = tid % G::TL;
-  team_fft<L, INV>(cols + team * LD, tw, lane, c0 + team < L);
+  team_fft<L, INV>(cols + team * LD, tw, lane, true);
   __syncthreads();
   for (int i = tid; i < CW * L; i += NT) {
     const int y = i / CW, c = i - y * CW;
-    if (c0 + c < L) data[(size_t)y * L + c0 + c] = cols[c * LD + y];
+    data[(size_t)y * L + c0 + c] = cols[c * LD + FftTeam<L>::pidx(y)];
   }
 }
 

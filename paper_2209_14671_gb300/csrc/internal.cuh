@@ -18,7 +18,7 @@ struct TileArgs {
   const int* row_xs;      // n: first support column of each pupil row (or 0)
   const int* row_cnt;     // n: support pixels in each pupil row
   const int* row_off;     // n: compact index of the first support pixel of each row
-  const float2* tw;       // n twiddles e^{-2 pi i k / n}
+  const float2* tw;       // n team twiddles tw[k1 * Q + l] = e^{-2 pi i l k1 / n}
   float2* G;              // K x S tile gradients on the support (gradient mode)
   double* costpart;       // K x CS fidelity cost partials
   float* I_out;           // K x n x n predicted intensities (simulate mode)
@@ -32,6 +32,15 @@ int tile_cluster_size(int n);
 size_t tile_smem_bytes(int n, int cs, int rowsA);
 cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
 cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------- FFT layout (see fft.cuh)
+// lanes per transform Q, and the padded buffer length L + L / Q
+inline int fft_team_lanes(int L) {
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  return 1 << (lg / 2);
+}
+inline int fft_padded_length(int L) { return L + L / fft_team_lanes(L); }
 
 // ---------------------------------------------------------------- big FFTs
 // 2D transforms of an L x L array: rows pass then columns pass, unnormalised.
@@ -94,6 +103,7 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring,
                                int* t_dev, double* out3, int advance, float* bc, double* gp, double g1,
                                double g2, cudaStream_t s);
+cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
                          double fixed_alpha, double fixed_beta, cudaStream_t s);

@@ -13,17 +13,20 @@
 namespace elf {
 
 // ------------------------------------------------------------------ helpers
+// Fixed-order block sum (1D or 2D blocks of whole warps, at most 8 warps);
+// the result is valid in the block's first thread.
 __device__ __forceinline__ double block_sum_double(double v, double* red) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int w = t >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[w] = v;
+  if ((t & 31) == 0) red[w] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0)
+  if (t == 0)
     for (int i = 0; i < nw; ++i) s += red[i];
-  return s;  // valid in thread 0
+  return s;
 }
 
 // Smoothed L1 of a 3-vector (reading A7): cost and omega = h / max(|h|, tau)
@@ -53,6 +56,7 @@ constexpr int HT = 32;            // output tile side
 constexpr int HA = HT + 4;        // amplitude/phase tile with a 2-pixel halo
 constexpr int HW = HT + 2;        // omega tile with a 1-pixel halo
 
+// Block of 32 x 8 threads per 32 x 32 output tile (2-pixel halo).
 __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   __shared__ float s_a[HA][HA + 1];
   __shared__ float s_p[HA][HA + 1];
@@ -60,58 +64,64 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   __shared__ double red[8];
   const int N = a.N;
   const int tx0 = blockIdx.x * HT, ty0 = blockIdx.y * HT;
-  const int tid = threadIdx.x;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
   const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
 
   // O = (-1)^(x+y) Ot / A; amplitude and phase (atan2, reading A12)
   for (int i = tid; i < HA * HA; i += 256) {
-    const int ly = i / HA, lx = i - ly * HA;
-    const int y = ty0 - 2 + ly, x = tx0 - 2 + lx;
-    float am = 0.f, ph = 0.f;
-    if (y >= 0 && y < N && x >= 0 && x < N) {
-      float2 o = a.ot[(size_t)y * N + x];
-      const float sg = ((x + y) & 1) ? -a.invA : a.invA;
-      o.x *= sg;
-      o.y *= sg;
-      am = sqrtf(cabs2(o));
-      ph = atan2f(o.y, o.x);
+    {
+      const int ly = i / HA, lx = i - ly * HA;
+      const int y = ty0 - 2 + ly, x = tx0 - 2 + lx;
+      float am = 0.f, ph = 0.f;
+      if (y >= 0 && y < N && x >= 0 && x < N) {
+        float2 o = a.ot[(size_t)y * N + x];
+        const float sg = ((x + y) & 1) ? -a.invA : a.invA;
+        o.x *= sg;
+        o.y *= sg;
+        am = sqrtf(cabs2(o));
+        ph = atan2f(o.y, o.x);
+      }
+      s_a[ly][lx] = am;
+      s_p[ly][lx] = ph;
     }
-    s_a[ly][lx] = am;
-    s_p[ly][lx] = ph;
   }
   __syncthreads();
 
-  // omega = H f / max(|H f|, tau) on the interior [1, N-2]^2, zero elsewhere
-  double ca = 0.0, cp = 0.0;
+  // omega = H f / max(|H f|, tau) on the interior [1, N-2]^2, zero elsewhere;
+  // per-thread cost partials in FP32 (a handful of pixels), block sums in FP64
+  float ca = 0.f, cp = 0.f;
   const float r2 = 1.41421356237309505f;
   for (int i = tid; i < HW * HW; i += 256) {
-    const int ly = i / HW, lx = i - ly * HW;
-    const int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
-    const int cy = ly + 1, cx = lx + 1;  // centre in the HA tile
-    float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (y >= 1 && y <= N - 2 && x >= 1 && x <= N - 2) {
-      float h0 = s_a[cy][cx - 1] - 2.f * s_a[cy][cx] + s_a[cy][cx + 1];
-      float h1 = s_a[cy - 1][cx] - 2.f * s_a[cy][cx] + s_a[cy + 1][cx];
-      float h2 = r2 * 0.25f * (s_a[cy + 1][cx + 1] - s_a[cy + 1][cx - 1] - s_a[cy - 1][cx + 1] + s_a[cy - 1][cx - 1]);
-      const float fa = huber3(h0, h1, h2, a.tau, a.iso);
-      float g0 = s_p[cy][cx - 1] - 2.f * s_p[cy][cx] + s_p[cy][cx + 1];
-      float g1 = s_p[cy - 1][cx] - 2.f * s_p[cy][cx] + s_p[cy + 1][cx];
-      float g2 = r2 * 0.25f * (s_p[cy + 1][cx + 1] - s_p[cy + 1][cx - 1] - s_p[cy - 1][cx + 1] + s_p[cy - 1][cx - 1]);
-      const float fp = huber3(g0, g1, g2, a.tau, a.iso);
-      w[0] = h0; w[1] = h1; w[2] = h2; w[3] = g0; w[4] = g1; w[5] = g2;
-      if (ly >= 1 && ly <= HT && lx >= 1 && lx <= HT) {  // owned pixel
-        ca += (double)fa;
-        cp += (double)fp;
+    {
+      const int ly = i / HW, lx = i - ly * HW;
+      const int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
+      const int cy = ly + 1, cx = lx + 1;  // centre in the HA tile
+      float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (y >= 1 && y <= N - 2 && x >= 1 && x <= N - 2) {
+        float h0 = s_a[cy][cx - 1] - 2.f * s_a[cy][cx] + s_a[cy][cx + 1];
+        float h1 = s_a[cy - 1][cx] - 2.f * s_a[cy][cx] + s_a[cy + 1][cx];
+        float h2 = r2 * 0.25f * (s_a[cy + 1][cx + 1] - s_a[cy + 1][cx - 1] - s_a[cy - 1][cx + 1] + s_a[cy - 1][cx - 1]);
+        const float fa = huber3(h0, h1, h2, a.tau, a.iso);
+        float g0 = s_p[cy][cx - 1] - 2.f * s_p[cy][cx] + s_p[cy][cx + 1];
+        float g1 = s_p[cy - 1][cx] - 2.f * s_p[cy][cx] + s_p[cy + 1][cx];
+        float g2 = r2 * 0.25f * (s_p[cy + 1][cx + 1] - s_p[cy + 1][cx - 1] - s_p[cy - 1][cx + 1] + s_p[cy - 1][cx - 1]);
+        const float fp = huber3(g0, g1, g2, a.tau, a.iso);
+        w[0] = h0; w[1] = h1; w[2] = h2; w[3] = g0; w[4] = g1; w[5] = g2;
+        if (ly >= 1 && ly <= HT && lx >= 1 && lx <= HT) {  // owned pixel
+          ca += fa;
+          cp += fp;
+        }
       }
-    }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s_w[k][ly][lx] = w[k];
+      for (int k = 0; k < 6; ++k) s_w[k][ly][lx] = w[k];
+    }
   }
   __syncthreads();
 
   // q = alpha O/(2 max(a,eta)) H^T omega_a + beta (i/2) O/(a^2+eta) H^T omega_phi
-  for (int i = tid; i < HT * HT; i += 256) {
-    const int ly = i / HT, lx = i - ly * HT;
+  for (int ly = ty; ly < HT; ly += 8) {
+    const int lx = tx;
     const int y = ty0 + ly, x = tx0 + lx;
     if (y >= N || x >= N) continue;
     const int wy = ly + 1, wx = lx + 1;
@@ -130,14 +140,15 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
     const float sg = ((x + y) & 1) ? -a.invA : a.invA;
     o.x *= sg;
     o.y *= sg;
-    const float ka = alpha * t[0] / (2.f * fmaxf(am, a.eta));
-    const float kp = beta * 0.5f * t[1] / (am * am + a.eta);
+    const float ka = __fdividef(alpha * t[0], 2.f * fmaxf(am, a.eta));
+    const float kp = __fdividef(beta * 0.5f * t[1], am * am + a.eta);
     // ka O + i kp O, then the forward-shift sign and 1/A
     float2 q = make_float2(ka * o.x - kp * o.y, ka * o.y + kp * o.x);
     a.q[(size_t)y * N + x] = cscale(q, sg);
   }
-  const double sa = block_sum_double(ca, red);
-  const double sp = block_sum_double(cp, red);
+  (void)tid;
+  const double sa = block_sum_double((double)ca, red);
+  const double sp = block_sum_double((double)cp, red);
   if (tid == 0) {
     const int b = blockIdx.y * gridDim.x + blockIdx.x;
     a.costpart[2 * b] = sa;
@@ -149,7 +160,7 @@ int hess_blocks(int N) { return ((N + HT - 1) / HT) * ((N + HT - 1) / HT); }
 
 cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s) {
   const int t = (a.N + HT - 1) / HT;
-  hessian_kernel<<<dim3(t, t), 256, 0, s>>>(a);
+  hessian_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -348,6 +359,20 @@ __global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int
       bc[1] = (float)(1.0 / (1.0 - p2));
     }
   }
+}
+
+// Running powers gamma^1 and bias corrections 1/(1 - gamma^1) of Eq. 19 for t = 0.
+__global__ void init_bias_kernel(float* bc, double* gp, double g1, double g2) {
+  if (threadIdx.x != 0) return;
+  gp[0] = g1;
+  gp[1] = g2;
+  bc[0] = (float)(1.0 / (1.0 - g1));
+  bc[1] = (float)(1.0 / (1.0 - g2));
+}
+
+cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s) {
+  init_bias_kernel<<<1, 32, 0, s>>>(bc, gp, g1, g2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring, int* t_dev,

@@ -93,15 +93,17 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int NTEAM = NT / TL;
   constexpr int CW = NL / CS;     // owned columns
   constexpr int WC = CW + 2;      // with one halo column per side
-  constexpr int LD = NL + 1;      // column pitch (padding against bank conflicts)
+  constexpr int RP = FftTeam<NL>::PADDED;  // FFT buffer length (padded layout)
+  constexpr int LD = RP + 1;      // column pitch of OC (odd: conflict-free across columns)
+  constexpr int LR = NL + 1;      // column pitch of R
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Itile = reinterpret_cast<float*>(smem_raw);      // NL x CW measured intensities (row-major)
   float2* tw = reinterpret_cast<float2*>(Itile + NL * CW);
-  float2* A1 = tw + NL;                                   // rowsA x NL band rows
-  float2* OC = A1 + a.rowsA * NL;                         // WC columns of pitch LD
-  float* R = reinterpret_cast<float*>(OC + WC * LD);      // WC columns of r
-  double* red = reinterpret_cast<double*>(R + ((WC * LD + 1) & ~1));
+  float2* A1 = tw + NL;                                   // rowsA band rows of pitch RP
+  float2* OC = A1 + a.rowsA * RP;                         // WC columns of pitch LD
+  float* R = reinterpret_cast<float*>(OC + WC * LD);      // WC columns of r, pitch LR
+  double* red = reinterpret_cast<double*>(R + ((WC * LR + 1) & ~1));
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, wl = tid & 31;
@@ -126,11 +128,6 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   for (int i = tid; i < NL; i += NT) tw[i] = a.tw[i];
-  // zero the non-band rows of every local column (the band rows arrive from the row owners)
-  for (int i = tid; i < WC * NL; i += NT) {
-    const int c = i / NL, y = i - c * NL;
-    if ((unsigned)(y - a.Blo) >= (unsigned)a.nb) OC[c * LD + y] = make_float2(0.f, 0.f);
-  }
   cluster_barrier<CS>();  // every CTA of the cluster is running before any remote store
 
   const int2 org = a.origin[led];
@@ -141,39 +138,41 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   for (int base = 0; base < a.rowsA; base += NTEAM) {
     const int lb = base + team;
     const bool act = lb < nrows;
-    float2* row = A1 + (act ? lb : 0) * NL;
+    float2* row = A1 + (act ? lb : 0) * RP;
     const int y = a.Blo + b0 + (act ? lb : 0);
+    const int py = FftTeam<NL>::pidx(y);
     if (act) {
       const int xs = a.row_xs[y], cnt = a.row_cnt[y];
       const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
       for (int x = lane; x < NL; x += TL) {
         float2 v = make_float2(0.f, 0.f);
         if ((unsigned)(x - xs) < (unsigned)cnt) v = cmul(a.pupil[y * NL + x], prow[x]);
-        row[x] = v;
+        row[FftTeam<NL>::pidx(x)] = v;
       }
     }
     __syncwarp();
     team_fft<NL, true>(row, tw, lane, act);
     if (act) {
       for (int x = lane; x < NL; x += TL) {
-        const float2 v = row[x];
+        const float2 v = row[FftTeam<NL>::pidx(x)];
         const int own = x / CW, c = x - own * CW + 1;
-        remote<CS>(OC, own)[c * LD + y] = v;
+        remote<CS>(OC, own)[c * LD + py] = v;
         if (CS > 1) {
-          if (c == CW && own + 1 < CS) remote<CS>(OC, own + 1)[0 * LD + y] = v;   // left halo of the next CTA
-          if (c == 1 && own > 0) remote<CS>(OC, own - 1)[(CW + 1) * LD + y] = v;  // right halo of the previous
+          if (c == CW && own + 1 < CS) remote<CS>(OC, own + 1)[0 * LD + py] = v;   // left halo of the next CTA
+          if (c == 1 && own > 0) remote<CS>(OC, own - 1)[(CW + 1) * LD + py] = v;  // right halo of the previous
         }
       }
     }
   }
   cluster_barrier<CS>();
 
-  // ---- B: inverse column transforms of the owned + halo columns (all local now)
+  // ---- B: inverse column transforms of the owned + halo columns (all local now);
+  // only the support band rows hold data, the rest are zeros the transform never reads
   for (int base = 0; base < WC; base += NTEAM) {
     const int lc = base + team;
     const int x = x0 - 1 + lc;
     const bool act = (lc < WC) && x >= 0 && x < NL;
-    team_fft<NL, true>(OC + (act ? lc : 0) * LD, tw, lane, act);
+    team_fft<NL, true>(OC + (act ? lc : 0) * LD, tw, lane, act, a.Blo, a.nb);
   }
   if (a.mode == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
@@ -181,17 +180,18 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // o = (-1)^(x+y) scale * IDFT, and the residual r.  Owned columns: lanes along x;
   // the two halo columns: threads along y.
   auto residual = [&](int y, int c, int x, float meas) {
-    float2 o = OC[c * LD + y];
+    const int py = FftTeam<NL>::pidx(y);
+    float2 o = OC[c * LD + py];
     const float sg = ((x + y) & 1) ? -a.scale : a.scale;
     o.x *= sg;
     o.y *= sg;
-    OC[c * LD + y] = o;
+    OC[c * LD + py] = o;
     const float m2 = cabs2(o);
     if (a.mode == 1) {
       if (c >= 1 && c <= CW) a.I_out[img + (size_t)y * NL + x] = m2;
       return;
     }
-    R[c * LD + y] = (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
+    R[c * LR + y] = (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
   };
   for (int y = warp; y < NL; y += NW)
     for (int cc = wl; cc < CW; cc += 32) residual(y, cc + 1, x0 + cc, a.mode == 0 ? Itile[y * CW + cc] : 0.f);
@@ -206,28 +206,45 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
 
   // W = o * nabla^T omega (Eq. 11) or o / (2 max(|o|, eta)) * nabla^T omega (Eq. 10),
   // times (-1)^(x+y) for the forward shift; cost phi summed over owned pixels.
-  double acc = 0.0;
-  const float tau = a.tau, tau2 = fmaxf(a.tau * a.tau, 1e-36f), hit = (a.tau > 0.f) ? 0.5f / a.tau : 0.f;
-  for (int y = warp; y < NL; y += NW) {
-    for (int cc = wl; cc < CW; cc += 32) {
-      const int c = cc + 1;
-      const int x = x0 + cc;
-      const OmegaOut w0 = omega_at<NL, LD>(R, y, x, c, tau, tau2, hit, a.iso);
-      float w = -w0.wx - w0.wy;
-      if (x >= 1) w += omega_at<NL, LD>(R, y, x - 1, c - 1, tau, tau2, hit, a.iso).wx;
-      if (y >= 1) w += omega_at<NL, LD>(R, y - 1, x, c, tau, tau2, hit, a.iso).wy;
-      acc += (double)w0.phi;
-      float2 o = OC[c * LD + y];
-      float f = w;
-      if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o)), a.eta));
-      if ((x + y) & 1) f = -f;
-      OC[c * LD + y] = cscale(o, f);
+  // Each warp walks a strip of rows with its lanes on the owned columns, so the
+  // normaliser is evaluated once per pixel: omega_x of the left neighbour comes
+  // from the lane to the left (lane 0 evaluates the halo column itself) and
+  // omega_y of the row above is carried in a register.
+  float acc = 0.f;  // per-thread partial of at most NL/NW pixels; block sum in FP64
+  {
+    static_assert(CW <= 32, "one warp spans the owned columns");
+    constexpr int RPW = NL / NW;  // rows per warp
+    const float tau = a.tau, tau2 = fmaxf(a.tau * a.tau, 1e-36f), hit = (a.tau > 0.f) ? 0.5f / a.tau : 0.f;
+    const bool on = wl < CW;
+    const int c = wl + 1, x = x0 + wl;
+    const int ybeg = warp * RPW;
+    float wy_prev = 0.f;
+    if (on && ybeg >= 1) wy_prev = omega_at<NL, LR>(R, ybeg - 1, x, c, tau, tau2, hit, a.iso).wy;
+    for (int y = ybeg; y < ybeg + RPW; ++y) {
+      OmegaOut w0 = {0.f, 0.f, 0.f};
+      if (on) w0 = omega_at<NL, LR>(R, y, x, c, tau, tau2, hit, a.iso);
+      float wx_left = __shfl_up_sync(0xffffffffu, w0.wx, 1);
+      if (wl == 0) wx_left = (x >= 1) ? omega_at<NL, LR>(R, y, x - 1, 0, tau, tau2, hit, a.iso).wx : 0.f;
+      if (on) {
+        float w = -w0.wx - w0.wy;
+        if (x >= 1) w += wx_left;
+        if (y >= 1) w += wy_prev;
+        acc += w0.phi;
+        const int py = FftTeam<NL>::pidx(y);
+        float2 o = OC[c * LD + py];
+        float f = w;
+        if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o)), a.eta));
+        if ((x + y) & 1) f = -f;
+        OC[c * LD + py] = cscale(o, f);
+      }
+      wy_prev = w0.wy;
     }
   }
-  // block reduction of the FP64 cost partial (fixed order)
+  // block reduction of the cost partials in FP64 (fixed order)
+  double accd = (double)acc;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if (wl == 0) red[warp] = acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if (wl == 0) red[warp] = accd;
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
@@ -244,8 +261,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   __syncthreads();
   for (int b = warp; b < a.nb; b += NW) {
     const int own = b / a.rowsA, lb = b - own * a.rowsA;
-    float2* dst = remote<CS>(A1, own) + lb * NL + x0;
-    for (int cc = wl; cc < CW; cc += 32) dst[cc] = OC[(cc + 1) * LD + a.Blo + b];
+    float2* dst = remote<CS>(A1, own) + lb * RP;
+    const int py = FftTeam<NL>::pidx(a.Blo + b);
+    for (int cc = wl; cc < CW; cc += 32) dst[FftTeam<NL>::pidx(x0 + cc)] = OC[(cc + 1) * LD + py];
   }
   cluster_barrier<CS>();
 
@@ -253,13 +271,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   for (int base = 0; base < a.rowsA; base += NTEAM) {
     const int lb = base + team;
     const bool act = lb < nrows;
-    float2* row = A1 + (act ? lb : 0) * NL;
+    float2* row = A1 + (act ? lb : 0) * RP;
     team_fft<NL, false>(row, tw, lane, act);
     if (act) {
       const int ky = a.Blo + b0 + lb;
       const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
       float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
-      for (int i = lane; i < cnt; i += TL) dst[i] = cscale(row[xs + i], a.scale);
+      for (int i = lane; i < cnt; i += TL) dst[i] = cscale(row[FftTeam<NL>::pidx(xs + i)], a.scale);
     }
   }
 }
@@ -283,8 +301,9 @@ static int tile_threads(int n) {
 }
 
 size_t tile_smem_bytes(int n, int cs, int rowsA) {
-  const size_t cw = n / cs, wc = cw + 2, ld = n + 1;
-  return 4 * (size_t)n * cw + 8 * ((size_t)n + (size_t)rowsA * n + wc * ld) + 4 * ((wc * ld + 1) & ~(size_t)1) +
+  const size_t rp = fft_padded_length(n);
+  const size_t cw = n / cs, wc = cw + 2, ld = rp + 1, lr = n + 1;
+  return 4 * (size_t)n * cw + 8 * ((size_t)n + (size_t)rowsA * rp + wc * ld) + 4 * ((wc * lr + 1) & ~(size_t)1) +
          8 * (size_t)(tile_threads(n) / 32);
 }
 

@@ -61,6 +61,14 @@ SIGNATURES = {
     "elf_set_tracing": (c_int, [c_void_p, c_int]),
     "elf_get_stage_times": (c_int, [c_void_p, P_float, c_int]),
     "elf_graph_kernel_count": (c_int, [c_void_p]),
+    "elf_server_create": (c_int, [ctypes.c_size_t, c_int, ctypes.POINTER(c_void_p)]),
+    "elf_server_submit": (c_int, [c_void_p, ctypes.POINTER(ElfProblem), ctypes.POINTER(ElfOptions), c_void_p, c_int,
+                                  ctypes.c_longlong]),
+    "elf_server_progress": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong), c_int, ctypes.POINTER(c_int)]),
+    "elf_server_result": (c_int, [c_void_p, ctypes.c_longlong, c_void_p]),
+    "elf_server_stats": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "elf_server_destroy": (None, [c_void_p]),
     "elf_estimate_weights_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "elf_destroy": (None, [c_void_p]),
     "elf_strerror": (ctypes.c_char_p, [c_int]),
