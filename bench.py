@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--serving-requests", type=int, default=120,
+                    help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
 
 
@@ -138,6 +140,59 @@ def make_inputs(w: dict, wid: int, torch, dev):
         I_clean = torch.empty((w["K"], w["n"], w["n"]), dtype=torch.float32, device=dev)
         sim.simulate(obj, I_clean)
     return IN.corrupt(I_clean.cpu().numpy(), wid, w)
+
+
+def serving_leg(args, torch, dev):
+    """Continuous-batching server on a Poisson stream of mixed reconstructions.
+
+    Requests: low-res side n in {64, 128, 256} x LED grid {7, 11, 15} (K = 49, 121, 225),
+    uniform mix, 50 iterations each, workload-0 optics, FP32, 150 GB device budget.
+    Arrivals: Poisson at 0.8 x the one-at-a-time capacity measured on the same mix.
+    Also a saturated run (all requests at t = 0) for throughput against the serial path."""
+    from paper_2209_14671_gb300 import elfpie as E
+    from paper_2209_14671_gb300 import serve as SV
+    R = args.serving_requests
+    classes = [(n, g) for n in (64, 128, 256) for g in (7, 11, 15)]
+    pool = {}
+    for ci, (n, g) in enumerate(classes):
+        w = IN.problem(0, grid=g, n=n)
+        sets = []
+        for v in range(2):
+            obj = torch.from_numpy(IN.object_field(100 + 10 * ci + v, w).astype(np.complex64)).to(dev)
+            with E.Elf(n, w["u"], w["k_xy_true"], w["na"], w["wavelength_um"], w["pixel_um"]) as sim:
+                Ic = torch.empty((w["K"], n, n), dtype=torch.float32, device=dev)
+                sim.simulate(obj, Ic)
+            I = IN.corrupt(Ic.cpu().numpy(), 0, w)
+            sets.append(torch.from_numpy(I).pin_memory().numpy())
+        pool[(n, g)] = (w, sets)
+    rng = IN.rng(4, IN.STREAM_ARRIVALS)
+    picks = rng.integers(0, len(classes), size=R)
+    reqs = []
+    for i, ci in enumerate(picks):
+        w, sets = pool[classes[ci]]
+        reqs.append(dict(n=w["n"], u=w["u"], k_xy=w["k_xy"].astype(np.float32), na=w["na"], wl=w["wavelength_um"],
+                         dx=w["pixel_um"], I=sets[i % 2], n_iter=50))
+    # warm-up: every shape once through both paths (handle creation, graph capture)
+    first = [reqs[list(picks).index(c)] for c in sorted(set(picks.tolist()))]
+    SV.run_serial(first)
+    budget = 150 << 30
+    with SV.Server(budget, max_active=32) as srv:
+        SV.run_stream(srv, first, np.zeros(len(first)))
+        serial_t, serial_total, _ = SV.run_serial(reqs)
+        cap = R / serial_total
+        gaps = rng.exponential(1.0 / (0.8 * cap), size=R)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        lat, makespan, _ = SV.run_stream(srv, reqs, arrivals)
+        _, sat_makespan, _ = SV.run_stream(srv, reqs, np.zeros(R))
+        st = srv.stats()
+    return {"requests": R, "mix": "n in {64,128,256} x K in {49,121,225}, 50 iterations each",
+            "arrival_rate_per_s": 0.8 * cap, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "tiles_per_s_at_load": R / makespan,
+            "saturated_tiles_per_s": R / sat_makespan, "serial_tiles_per_s": cap,
+            "saturated_speedup_vs_serial": (R / sat_makespan) / cap,
+            "serial_p50_ms": float(np.percentile(serial_t, 50) * 1e3),
+            "handles_created": st["handles_created"], "device_bytes": st["used_bytes"],
+            "budget_bytes": budget}
 
 
 def run_reference(args):
@@ -272,6 +327,10 @@ def run_ours(args):
                "step": f"one reconstruction: elf_set_measurements(pinned host) + elf_step({iters}) + "
                        f"elf_get_object(pinned host); {jobs} jobs timed by wall clock"}
 
+    serving = None
+    if args.serving_requests > 0:
+        serving = serving_leg(args, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, its, el = oracle_sample_rate(I_host, w, args.cpu_seconds)
@@ -298,6 +357,7 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "e2e": e2e,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

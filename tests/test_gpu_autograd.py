@@ -6,10 +6,13 @@ At the workload sizes of the differentiation check (64 x 64 images, 7 x 7 LEDs,
     (relative L2 2e-3, as the other gradient parity tests);
   * central finite differences of the GPU cost along 32 seeded complex
     directions (for Psi and for P) match 2 Re<g, d>: Richardson-extrapolated
-    central differences with steps 2e-3 and 1e-3 of |Psi| (the FP32 cost's
-    rounding noise, ~1e-8 of L, divided by the step must stay well below the
-    directional derivative); bound 2e-2 per direction, median 2e-3.  The smoothing radii are 1e-3 here, as in the
-    oracle's finite-difference pins, so the cost is smooth at that step.
+    central differences with steps 2e-3 and 1e-3 of |Psi|; bound 1e-2 per
+    direction, median 1e-3.  FP32 cannot resolve steps much below 1e-3 of
+    |Psi|, and with the default smoothing radii the Huber-smoothed L1 terms
+    curve on a scale of tau, so the FP64 oracle's own differences only converge
+    at steps near 1e-6; this check therefore uses tau = 0.1 (any tau is a valid
+    test of the gradient code), where the FP64 differences at these steps are
+    within 1e-4.
 """
 import numpy as np
 import pytest
@@ -25,24 +28,37 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 OPTS = dict(tau_fid=1e-3, tau_h=1e-3)
+OPTS_FD = dict(tau_fid=0.1, tau_h=0.1)
 
 
-@pytest.fixture(scope="module")
-def setup():
+def _setup(opts):
     B.build()
     E.load()
     from paper_2209_14671_gb300.autograd import ElfCost
     c = case("w2")
     I = c["I"].astype(np.float64)
-    opt = O.Options(**OPTS)
+    opt = O.Options(**opts)
     st = O.init_state(I, c["geo"], c["k_xy"], opt)
     st, _ = O.run(st, I, c["geo"], opt, 3)
     st = oracle_state_to_f32(st)
-    elf = E.Elf(c["n"], c["u"], c["k_xy"], c["na"], c["wl"], c["dx"], options=OPTS)
+    elf = E.Elf(c["n"], c["u"], c["k_xy"], c["na"], c["wl"], c["dx"], options=opts)
     elf.set_measurements(c["I"])
     load_state(elf, st)
-    yield c, st, opt, elf, ElfCost(elf)
-    elf.close()
+    return c, st, opt, elf, ElfCost(elf)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    r = _setup(OPTS)
+    yield r
+    r[3].close()
+
+
+@pytest.fixture(scope="module")
+def setup_fd():
+    r = _setup(OPTS_FD)
+    yield r
+    r[3].close()
 
 
 def test_autograd_gradients_match_oracle(setup):
@@ -63,8 +79,8 @@ def test_autograd_gradients_match_oracle(setup):
     assert e_L < 1e-5 and e_psi < 2e-3 and e_p < 2e-3
 
 
-def test_autograd_matches_central_differences(setup):
-    c, st, opt, elf, cost = setup
+def test_autograd_matches_central_differences(setup_fd):
+    c, st, opt, elf, cost = setup_fd
     dev = torch.device("cuda:0")
     psi0 = st.psi
     pup0 = st.pupil
@@ -96,4 +112,4 @@ def test_autograd_matches_central_differences(setup):
             errs.append(abs(fd - an) / abs(an))
     errs = np.array(errs)
     print(f"finite differences: median {np.median(errs):.2e} max {errs.max():.2e}")
-    assert np.median(errs) < 2e-3 and errs.max() < 2e-2
+    assert np.median(errs) < 1e-3 and errs.max() < 1e-2
