@@ -55,36 +55,11 @@ __device__ __forceinline__ T* remote(T* p, int rank) {
   }
 }
 
+// The smoothed normaliser of Eq. 12 (reading A7) at one pixel: omega = d / max(|d|, tau),
+// phi = |d| (|d| >= tau) or |d|^2/(2 tau) + tau/2 (per component when anisotropic).
 struct OmegaOut {
   float wx, wy, phi;
 };
-
-// Smoothed normaliser of Eq. 12 (reading A7) at pixel (y, x) from the residual r
-// stored column-major in R (local column c = x - x0 + 1, pitch LD):
-//   omega = d / max(|d|, tau), phi = |d| (|d| >= tau) or |d|^2/(2 tau) + tau/2.
-// tau2 = tau^2 floored at 1e-36 so that d = 0 gives omega = 0 even for tau = 0.
-template <int NL, int LD>
-__device__ __forceinline__ OmegaOut omega_at(const float* R, int y, int x, int c, float tau, float tau2,
-                                             float half_inv_tau, int iso) {
-  const float r0 = R[c * LD + y];
-  const float dx = (x < NL - 1) ? R[(c + 1) * LD + y] - r0 : 0.f;
-  const float dy = (y < NL - 1) ? R[c * LD + y + 1] - r0 : 0.f;
-  OmegaOut o;
-  if (iso) {
-    const float ss = dx * dx + dy * dy;
-    const float inv = rsqrtf(fmaxf(ss, tau2));
-    o.wx = dx * inv;
-    o.wy = dy * inv;
-    o.phi = (ss >= tau * tau) ? ss * inv : ss * half_inv_tau + 0.5f * tau;
-  } else {
-    const float ax = fabsf(dx), ay = fabsf(dy);
-    o.wx = dx / fmaxf(ax, tau);
-    o.wy = dy / fmaxf(ay, tau);
-    o.phi = ((ax >= tau) ? ax : ax * ax * half_inv_tau + 0.5f * tau) +
-            ((ay >= tau) ? ay : ay * ay * half_inv_tau + 0.5f * tau);
-  }
-  return o;
-}
 
 template <int NL, int CS, int NT>
 __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
@@ -95,15 +70,15 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int WC = CW + 2;      // with one halo column per side
   constexpr int RP = FftTeam<NL>::PADDED;  // FFT buffer length (padded layout)
   constexpr int LD = RP + 1;      // column pitch of OC (odd: conflict-free across columns)
-  constexpr int LR = NL + 1;      // column pitch of R
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Itile = reinterpret_cast<float*>(smem_raw);      // NL x CW measured intensities (row-major)
-  float2* tw = reinterpret_cast<float2*>(Itile + NL * CW);
+  float* Ihalo = Itile + NL * CW;                          // 2 x NL: the halo columns x0-1, x0+CW
+  float2* tw = reinterpret_cast<float2*>(Ihalo + 2 * NL);
   float2* A1 = tw + NL;                                   // rowsA band rows of pitch RP
   float2* OC = A1 + a.rowsA * RP;                         // WC columns of pitch LD
-  float* R = reinterpret_cast<float*>(OC + WC * LD);      // WC columns of r, pitch LR
-  double* red = reinterpret_cast<double*>(R + ((WC * LR + 1) & ~1));
+  float* Hx = reinterpret_cast<float*>(OC + WC * LD);     // 2 x NL: r at x0+CW, omega_x at x0-1
+  double* red = reinterpret_cast<double*>(Hx + 2 * NL);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, wl = tid & 31;
@@ -123,6 +98,14 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       const int y = i / CH, k = i - y * CH;
       const float* src = a.meas + img + (size_t)y * NL + x0 + 4 * k;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 4u * (y * CW + 4 * k)), "l"(src)
+                   : "memory");
+    }
+    for (int i = tid; i < 2 * NL; i += NT) {
+      const int side = i / NL, y = i - side * NL;
+      const int x = side ? x0 + CW : x0 - 1;
+      if (x < 0 || x >= NL) continue;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sbase + 4u * (NL * CW + i)),
+                   "l"(a.meas + img + (size_t)y * NL + x)
                    : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -177,67 +160,120 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   if (a.mode == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
-  // o = (-1)^(x+y) scale * IDFT, and the residual r.  Owned columns: lanes along x;
-  // the two halo columns: threads along y.
-  auto residual = [&](int y, int c, int x, float meas) {
-    const int py = FftTeam<NL>::pidx(y);
-    float2 o = OC[c * LD + py];
+  // o = (-1)^(x+y) scale * IDFT (register values; the raw transform stays in OC)
+  auto load_o = [&](int y, int c, int x) -> float2 {
+    const float2 o = OC[c * LD + FftTeam<NL>::pidx(y)];
     const float sg = ((x + y) & 1) ? -a.scale : a.scale;
-    o.x *= sg;
-    o.y *= sg;
-    OC[c * LD + py] = o;
-    const float m2 = cabs2(o);
-    if (a.mode == 1) {
-      if (c >= 1 && c <= CW) a.I_out[img + (size_t)y * NL + x] = m2;
-      return;
-    }
-    R[c * LR + y] = (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
+    return make_float2(o.x * sg, o.y * sg);
   };
-  for (int y = warp; y < NL; y += NW)
-    for (int cc = wl; cc < CW; cc += 32) residual(y, cc + 1, x0 + cc, a.mode == 0 ? Itile[y * CW + cc] : 0.f);
-  for (int i = tid; i < 2 * NL; i += NT) {
-    const int c = (i < NL) ? 0 : CW + 1;
-    const int y = i & (NL - 1);
-    const int x = x0 - 1 + c;
-    if (x >= 0 && x < NL) residual(y, c, x, a.mode == 0 ? a.meas[img + (size_t)y * NL + x] : 0.f);
+  if (a.mode == 1) {  // forward model only: |o|^2 on the owned columns
+    for (int y = warp; y < NL; y += NW)
+      for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1, x0 + cc));
+    return;  // no remote access after the last cluster barrier
   }
-  if (a.mode == 1) return;  // no remote access after the last cluster barrier
-  __syncthreads();
+  // residual r = |o|^2 - I (Eq. 5) or |o| - sqrt(max(I, 0)) (Eq. 4)
+  auto resid = [&](float2 o, float meas) -> float {
+    const float m2 = cabs2(o);
+    return (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
+  };
 
   // W = o * nabla^T omega (Eq. 11) or o / (2 max(|o|, eta)) * nabla^T omega (Eq. 10),
   // times (-1)^(x+y) for the forward shift; cost phi summed over owned pixels.
-  // Each warp walks a strip of rows with its lanes on the owned columns, so the
-  // normaliser is evaluated once per pixel: omega_x of the left neighbour comes
-  // from the lane to the left (lane 0 evaluates the halo column itself) and
-  // omega_y of the row above is carried in a register.
+  // Each warp walks a strip of rows with its lanes on the owned columns, carrying
+  // r, o and omega_y of the neighbouring rows in registers: the residual and the
+  // normaliser are evaluated once per pixel, x-neighbours come by shuffle and the
+  // halo columns are evaluated by the edge lanes.  The rows just outside the strip
+  // are read before a block barrier, because their owners overwrite them with W.
   float acc = 0.f;  // per-thread partial of at most NL/NW pixels; block sum in FP64
   {
     static_assert(CW <= 32, "one warp spans the owned columns");
     constexpr int RPW = NL / NW;  // rows per warp
     const float tau = a.tau, tau2 = fmaxf(a.tau * a.tau, 1e-36f), hit = (a.tau > 0.f) ? 0.5f / a.tau : 0.f;
     const bool on = wl < CW;
-    const int c = wl + 1, x = x0 + wl;
-    const int ybeg = warp * RPW;
+    const int cc = on ? wl : 0;
+    const int c = cc + 1, x = x0 + cc;
+    const bool has_left = x0 >= 1, has_right = x0 + CW < NL;
+    const int ybeg = warp * RPW, yend = ybeg + RPW;
+    auto r_own = [&](int y) { return resid(load_o(y, c, x), Itile[y * CW + cc]); };
+    auto r_left = [&](int y) { return resid(load_o(y, 0, x0 - 1), Ihalo[y]); };
+    auto r_right = [&](int y) { return resid(load_o(y, CW + 1, x0 + CW), Ihalo[NL + y]); };
+    auto huber2 = [&](float dx, float dy) -> OmegaOut {
+      OmegaOut o;
+      if (a.iso) {
+        const float ss = dx * dx + dy * dy;
+        const float inv = rsqrtf(fmaxf(ss, tau2));
+        o.wx = dx * inv;
+        o.wy = dy * inv;
+        o.phi = (ss >= tau * tau) ? ss * inv : ss * hit + 0.5f * tau;
+      } else {
+        const float ax = fabsf(dx), ay = fabsf(dy);
+        o.wx = dx / fmaxf(ax, tau);
+        o.wy = dy / fmaxf(ay, tau);
+        o.phi = ((ax >= tau) ? ax : ax * ax * hit + 0.5f * tau) + ((ay >= tau) ? ay : ay * ay * hit + 0.5f * tau);
+      }
+      return o;
+    };
+    // halo tables: r at the right halo column and omega_x at the left halo column, every row
+    for (int y = tid; y < NL; y += NT) {
+      Hx[y] = has_right ? r_right(y) : 0.f;
+      float wl_x = 0.f;
+      if (has_left) {
+        const float rl = r_left(y);
+        const float dxl = resid(load_o(y, 1, x0), Itile[y * CW]) - rl;
+        const float dyl = (y < NL - 1) ? r_left(y + 1) - rl : 0.f;
+        wl_x = huber2(dxl, dyl).wx;
+      }
+      Hx[NL + y] = wl_x;
+    }
+    // rows outside the strip, read before the barrier
+    const float r_above = (ybeg >= 1) ? r_own(ybeg - 1) : 0.f;
+    const float r_below = (yend < NL) ? r_own(yend) : 0.f;
+    __syncthreads();
+    float2 o_cur = load_o(ybeg, c, x);
+    float r_cur = resid(o_cur, Itile[ybeg * CW + cc]);
+    // omega_y at the row above the strip
     float wy_prev = 0.f;
-    if (on && ybeg >= 1) wy_prev = omega_at<NL, LR>(R, ybeg - 1, x, c, tau, tau2, hit, a.iso).wy;
-    for (int y = ybeg; y < ybeg + RPW; ++y) {
-      OmegaOut w0 = {0.f, 0.f, 0.f};
-      if (on) w0 = omega_at<NL, LR>(R, y, x, c, tau, tau2, hit, a.iso);
+    if (ybeg >= 1) {
+      float rr = __shfl_down_sync(0xffffffffu, r_above, 1);
+      if (wl == CW - 1) rr = Hx[ybeg - 1];
+      const float dx = (x < NL - 1) ? rr - r_above : 0.f;
+      wy_prev = huber2(dx, r_cur - r_above).wy;
+    }
+    // one row of look-ahead held in registers, loaded an iteration before it is used
+    float2 o_nxt = (ybeg + 1 < yend) ? load_o(ybeg + 1, c, x) : make_float2(0.f, 0.f);
+    float i_nxt = (ybeg + 1 < yend) ? Itile[(ybeg + 1) * CW + cc] : 0.f;
+#pragma unroll 2
+    for (int y = ybeg; y < yend; ++y) {
+      // loads for row y + 2 (consumed next iteration)
+      float2 o_nn = make_float2(0.f, 0.f);
+      float i_nn = 0.f;
+      if (y + 2 < yend) {
+        o_nn = load_o(y + 2, c, x);
+        i_nn = Itile[(y + 2) * CW + cc];
+      }
+      const float r_nxt = (y + 1 < yend) ? resid(o_nxt, i_nxt) : ((y + 1 < NL) ? r_below : 0.f);
+      float rr = __shfl_down_sync(0xffffffffu, r_cur, 1);
+      if (wl == CW - 1) rr = Hx[y];
+      const float dx = (x < NL - 1) ? rr - r_cur : 0.f;
+      const float dy = (y < NL - 1) ? r_nxt - r_cur : 0.f;
+      const OmegaOut w0 = huber2(dx, dy);
       float wx_left = __shfl_up_sync(0xffffffffu, w0.wx, 1);
-      if (wl == 0) wx_left = (x >= 1) ? omega_at<NL, LR>(R, y, x - 1, 0, tau, tau2, hit, a.iso).wx : 0.f;
+      if (wl == 0) wx_left = Hx[NL + y];
       if (on) {
         float w = -w0.wx - w0.wy;
         if (x >= 1) w += wx_left;
         if (y >= 1) w += wy_prev;
         acc += w0.phi;
-        const int py = FftTeam<NL>::pidx(y);
-        float2 o = OC[c * LD + py];
         float f = w;
-        if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o)), a.eta));
-        if ((x + y) & 1) f = -f;
-        OC[c * LD + py] = cscale(o, f);
+        if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
+        // W times (-1)^(x+y) for the forward fftshift; o_cur already carries the inverse one
+        OC[c * LD + FftTeam<NL>::pidx(y)] = cscale(o_cur, ((x + y) & 1) ? -f : f);
       }
       wy_prev = w0.wy;
+      o_cur = o_nxt;
+      r_cur = r_nxt;
+      o_nxt = o_nn;
+      i_nxt = i_nn;
     }
   }
   // block reduction of the cost partials in FP64 (fixed order)
@@ -302,8 +338,8 @@ static int tile_threads(int n) {
 
 size_t tile_smem_bytes(int n, int cs, int rowsA) {
   const size_t rp = fft_padded_length(n);
-  const size_t cw = n / cs, wc = cw + 2, ld = rp + 1, lr = n + 1;
-  return 4 * (size_t)n * cw + 8 * ((size_t)n + (size_t)rowsA * rp + wc * ld) + 4 * ((wc * lr + 1) & ~(size_t)1) +
+  const size_t cw = n / cs, wc = cw + 2, ld = rp + 1;
+  return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + wc * ld) + 4 * 2 * (size_t)n +
          8 * (size_t)(tile_threads(n) / 32);
 }
 
