@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision leg")
     ap.add_argument("--serving-requests", type=int, default=120,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
@@ -195,6 +196,45 @@ def serving_leg(args, torch, dev):
             "budget_bytes": budget}
 
 
+def precision_leg(torch, dev):
+    """Tensor-core tile transforms (BF16 3-term split, FP32 accumulation) against the FP32
+    FFT path on the 128 x 128 / 225-LED / 512 x 512 workload: time per iteration, tile
+    stage time, achieved tensor FLOP/s of the tile GEMMs, and the relative L2 difference
+    of the two paths' spectra after 20 iterations from the same initial state."""
+    from paper_2209_14671_gb300 import elfpie as E
+    w = IN.problem(3)
+    I_dev = torch.from_numpy(make_inputs(w, 3, torch, dev)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    psi = {}
+    for td in (0, 1):
+        elf = E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"],
+                    options=dict(tile_dft=td), stream=stream)
+        elf.set_measurements(I_dev)
+        elf.step(20)
+        psi[td] = elf.get_spectrum()
+        elf.set_tracing(True)
+        for _ in range(3):
+            elf.step(1)
+        t_it, t_tile = [], []
+        for _ in range(10):
+            elf.step(1)
+            st = elf.stage_times()
+            t_it.append(st["iteration"])
+            t_tile.append(st["tile"])
+        res[td] = (float(np.median(t_it)), float(np.median(t_tile)))
+        elf.close()
+    # tile GEMM work per LED (M padded to 128): 2 M (2 N) (6 K) over the four products
+    flop = w["K"] * 2 * 128 * (256 * 384 + 256 * 384 + 256 * 768 + 128 * 768)
+    diff = float(np.linalg.norm(psi[1] - psi[0]) / np.linalg.norm(psi[0]))
+    return {"workload": w["name"], "fp32_fft_ms_per_iter": res[0][0], "tensor_core_ms_per_iter": res[1][0],
+            "fp32_fft_tile_ms": res[0][1], "tensor_core_tile_ms": res[1][1],
+            "speedup_iteration": res[0][0] / res[1][0], "speedup_tile": res[0][1] / res[1][1],
+            "tile_gemm_tflops": flop / (res[1][1] * 1e-3) / 1e12,
+            "rel_l2_psi_tc_vs_fp32_after_20_iterations": diff,
+            "note": "error vs the FP64 oracle: tests/test_gpu_precision.py"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -327,6 +367,10 @@ def run_ours(args):
                "step": f"one reconstruction: elf_set_measurements(pinned host) + elf_step({iters}) + "
                        f"elf_get_object(pinned host); {jobs} jobs timed by wall clock"}
 
+    precision = None
+    if not args.no_precision and world == 1:
+        precision = precision_leg(torch, dev)
+
     serving = None
     if args.serving_requests > 0:
         serving = serving_leg(args, torch, dev)
@@ -358,6 +402,7 @@ def run_ours(args):
             "gpu_launches": kernels_per_step * args.steps,
             "e2e": e2e,
             "serving": serving,
+            "precision": precision,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

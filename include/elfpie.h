@@ -44,7 +44,7 @@ enum {
   ELF_ENOMEM = -2,    /* device allocation failed */
   ELF_ECUDA = -3,     /* a CUDA runtime call failed; see elf_last_error() */
   ELF_ENUMERIC = -4,  /* a non-finite cost was produced */
-  ELF_ETIMEOUT = -5,  /* a bounded wait ran out */
+  ELF_ETIMEOUT = -5,  /* a bounded device wait ran out (tensor-core path); the results are invalid */
   ELF_ESTATE = -6     /* call out of order (e.g. elf_step before elf_set_measurements) */
 };
 
@@ -81,6 +81,8 @@ typedef struct {
   double eta_h;      /* Eq. 14 eta and the |O| floor of Eq. 13 (1e-12) */
   double tau_fid;    /* smoothing radius of the L1 fidelity (1e-6) */
   double tau_h;      /* smoothing radius of the Hessian L1 terms (1e-4) */
+  int tile_dft;      /* tile transforms: 0 = FP32 FFT (default); 1 = tensor-core DFT, BF16 3-term split with
+                        FP32 accumulation (not in the paper; n_lowres = 128 with the support band <= 64 only) */
 } elf_options;
 
 /* Full optimiser state of Eq. 19 for Psi and P (Algorithm 1 keeps nothing else).

@@ -82,6 +82,10 @@ struct elf_handle_s {
          *out3 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
   size_t device_bytes = 0;  // sum of this handle's device allocations
+  // tensor-core tile path (tile_dft = 1)
+  float2 *tc_X = nullptr, *tc_Y = nullptr, *tc_O = nullptr, *tc_W = nullptr, *tc_Z = nullptr, *tc_G = nullptr;
+  float2 *tc_Einv = nullptr, *tc_Ffwd = nullptr;
+  int* tc_err = nullptr;
   float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
   double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
   std::vector<void*> allocs;
@@ -188,7 +192,41 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ta.iso = h->opt.omega_iso;
   ta.mode = 0;
   ELF_MARK(s0, ELF_STAGE_TILE, 0);
-  ELF_CK(launch_tile(ta, h->n, s0));
+  if (h->opt.tile_dft) {
+    TcArgs tc{};
+    tc.psi = psi;
+    tc.pupil = pupil;
+    tc.origin = h->origin;
+    tc.row_xs = h->row_xs;
+    tc.row_cnt = h->row_cnt;
+    tc.row_off = h->row_off;
+    tc.meas = h->I;
+    tc.Einv = h->tc_Einv;
+    tc.Ffwd = h->tc_Ffwd;
+    tc.X = h->tc_X;
+    tc.Y = h->tc_Y;
+    tc.O = h->tc_O;
+    tc.Wt = h->tc_W;
+    tc.Z = h->tc_Z;
+    tc.Gt = h->tc_G;
+    tc.G = h->G;
+    tc.costpart = h->cost_fid;
+    tc.err = h->tc_err;
+    tc.n = h->n;
+    tc.N = h->N;
+    tc.K = h->K;
+    tc.S = h->S;
+    tc.Blo = h->Blo;
+    tc.nb = h->nb;
+    tc.scale = ta.scale;
+    tc.tau = ta.tau;
+    tc.eta = ta.eta;
+    tc.fidelity = ta.fidelity;
+    tc.iso = ta.iso;
+    ELF_CK(launch_tc_tile(tc, s0));
+  } else {
+    ELF_CK(launch_tile(ta, h->n, s0));
+  }
   ELF_MARK(s0, ELF_STAGE_TILE, 1);
 
   PupilArgs pa{};
@@ -263,7 +301,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 1);
   }
   ELF_MARK(s0, ELF_STAGE_COST, 0);
-  ELF_CK(launch_cost_reduce(h->cost_fid, h->K * h->cs, h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
+  ELF_CK(launch_cost_reduce(h->cost_fid, h->opt.tile_dft ? h->K : h->K * h->cs, h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
                             h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, h->bc, h->gp,
                             h->opt.gamma1, h->opt.gamma2, s0));
   ELF_MARK(s0, ELF_STAGE_COST, 1);
@@ -347,6 +385,7 @@ int elf_default_options(elf_options* o) {
   o->eta_h = 1e-12;
   o->tau_fid = 1e-6;
   o->tau_h = 1e-4;
+  o->tile_dft = 0;
   return ELF_OK;
 }
 
@@ -382,7 +421,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   const elf_options& op = h->opt;
   if (!(op.gamma1 >= 0 && op.gamma1 < 1 && op.gamma2 >= 0 && op.gamma2 < 1 && op.tau_fid >= 0 && op.tau_h >= 0 &&
         op.eta_opt >= 0 && op.eta_h >= 0 && op.s0_psi >= 0 && op.s0_pupil >= 0 && std::isfinite(op.alpha) &&
-        std::isfinite(op.beta) && (op.fidelity == 0 || op.fidelity == 1)))
+        std::isfinite(op.beta) && (op.fidelity == 0 || op.fidelity == 1) && (op.tile_dft == 0 || op.tile_dft == 1)))
     return set_error(ELF_EINVAL, "invalid options");
   h->n = n;
   h->u = u;
@@ -436,6 +475,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   h->S = S;
   h->Blo = Blo;
   h->nb = Bhi - Blo + 1;
+  if (h->opt.tile_dft && (n != kTcN || h->nb > kTcBand))
+    return set_error(ELF_EINVAL, "tile_dft = 1 needs n_lowres = 128 and a support band of at most 64 rows");
   h->cs = tile_cluster_size(n);
   h->rowsA = (h->nb + h->cs - 1) / h->cs;
   h->Q = pupil_chunks(K, S);
@@ -519,6 +560,29 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->flag, 1))) return rc;
   if ((rc = dalloc(h, &h->bc, 2))) return rc;
   if ((rc = dalloc(h, &h->gp, 2))) return rc;
+  if (h->opt.tile_dft) {
+    const size_t Kz = (size_t)K;
+    if ((rc = dalloc(h, &h->tc_X, Kz * kTcBand * kTcBand))) return rc;
+    if ((rc = dalloc(h, &h->tc_Y, Kz * kTcBand * kTcN))) return rc;
+    if ((rc = dalloc(h, &h->tc_O, Kz * kTcN * kTcN))) return rc;
+    if ((rc = dalloc(h, &h->tc_W, Kz * kTcN * kTcN))) return rc;
+    if ((rc = dalloc(h, &h->tc_Z, Kz * kTcBand * kTcN))) return rc;
+    if ((rc = dalloc(h, &h->tc_G, Kz * kTcBand * kTcBand))) return rc;
+    if ((rc = dalloc(h, &h->tc_err, 1))) return rc;
+    // band DFT matrices in FP64: rows j < nb hold frequency Blo + j, the rest are zero
+    std::vector<float2> Ei((size_t)kTcBand * kTcN, make_float2(0.f, 0.f)), Ff(Ei);
+    const double pi = 3.14159265358979323846;
+    for (int j = 0; j < h->nb; ++j)
+      for (int x = 0; x < kTcN; ++x) {
+        const double ang = 2.0 * pi * (double)(((long)(h->Blo + j) * x) % kTcN) / (double)kTcN;
+        Ei[(size_t)j * kTcN + x] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        Ff[(size_t)j * kTcN + x] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+      }
+    if ((rc = upload(h, &h->tc_Einv, Ei))) return rc;
+    if ((rc = upload(h, &h->tc_Ffwd, Ff))) return rc;
+    ELF_CK(cudaMemset(h->tc_err, 0, sizeof(int)));
+    ELF_CK(prepare_tc());
+  }
   ELF_CK(prepare_tile(n, h->rowsA));
   ELF_CK(prepare_fft(n));
   ELF_CK(prepare_fft(N));
@@ -660,6 +724,11 @@ int elf_get_costs(elf_handle h, double* out, int max_iter) {
   int t = 0;
   ELF_CK(cudaMemcpyAsync(&t, h->t_dev, sizeof(int), cudaMemcpyDeviceToHost, h->user));
   ELF_CK(cudaStreamSynchronize(h->user));
+  if (h->tc_err) {
+    int bad = 0;
+    ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) return set_error(ELF_ETIMEOUT, "a tensor-core wait ran out; results are invalid");
+  }
   int count = t < max_iter ? t : max_iter;
   if (count > kCostRing) count = kCostRing;
   std::vector<double> ring(3 * kCostRing);
@@ -745,6 +814,11 @@ int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* co
   double c[3];
   ELF_CK(cudaMemcpyAsync(c, h->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ELF_CK(cudaStreamSynchronize(s));
+  if (h->tc_err) {
+    int bad = 0;
+    ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) return set_error(ELF_ETIMEOUT, "a tensor-core wait ran out; results are invalid");
+  }
   if (costs3) std::memcpy(costs3, c, sizeof(c));
   for (double v : c)
     if (!std::isfinite(v)) return set_error(ELF_ENUMERIC, "non-finite cost");

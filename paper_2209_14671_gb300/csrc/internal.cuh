@@ -33,6 +33,26 @@ size_t tile_smem_bytes(int n, int cs, int rowsA);
 cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
 cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
 
+// ---------------------------------------------------------------- tensor-core tile path (tc_dft.cu)
+constexpr int kTcN = 128;     // tile side of the tensor-core path
+constexpr int kTcBand = 64;   // padded band of support rows / columns
+struct TcArgs {
+  const float2* psi; const float2* pupil; const int2* origin;
+  const int* row_xs; const int* row_cnt; const int* row_off;
+  const float* meas;
+  const float2* Einv;   // 64 x 128: e^{+2 pi i (Blo + j) x / n}, zero rows j >= nb
+  const float2* Ffwd;   // 64 x 128: e^{-2 pi i (Blo + j) x / n}, zero rows j >= nb
+  float2 *X, *Y, *O, *Wt, *Z, *Gt;  // per-LED intermediates
+  float2* G;            // K x S output on the support
+  double* costpart;     // K fidelity cost partials
+  int* err;             // set when a bounded wait runs out
+  int n, N, K, S, Blo, nb;
+  float scale, tau, eta;
+  int fidelity, iso;
+};
+cudaError_t prepare_tc();
+cudaError_t launch_tc_tile(const TcArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- FFT layout (see fft.cuh)
 // lanes per transform Q, and the padded buffer length L + L / Q
 inline int fft_team_lanes(int L) {

@@ -52,6 +52,7 @@ def _create(n=64, u=4, k=((0.0, 0.0),), na=0.1, wl=0.63, dx=1.625, **opts):
     (dict(wl=0.0), "wavelength_um"),
     (dict(k=((float("nan"), 0.0),)), "non-finite"),
     (dict(gamma1=1.5), "invalid options"),
+    (dict(n=64, tile_dft=1), "tile_dft"),            # the tensor-core tile path is for n = 128
 ])
 def test_invalid_problems_are_rejected(lib, kw, needle):
     rc, msg = _create(**kw)
