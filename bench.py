@@ -59,6 +59,17 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's time (the job's time when every rank runs its own replica)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def tile_sources_hash() -> str:
     h = hashlib.sha256()
     for p in TILE_SOURCES:
@@ -316,11 +327,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     units = w["K"] * args.steps * world
     value = units / (total_ms / 1e3)
@@ -357,11 +365,7 @@ def run_ours(args):
             elf.set_measurements(I_pin.numpy())   # H2D of the job's measurements + initial state
             elf.step(iters)
             elf.get_object(O_pin.numpy())         # D2H of the reconstructed object (synchronises)
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": w["K"] * iters * jobs * world / el, "unit": UNIT,
                "h2d_bytes_per_step": int(I_host.nbytes), "d2h_bytes_per_step": int(O_pin.numel() * 8),
                "step": f"one reconstruction: elf_set_measurements(pinned host) + elf_step({iters}) + "

@@ -140,8 +140,17 @@ __global__ void __launch_bounds__(kTcThreads) tc_cgemm_kernel(const CgemmArgs a)
     const int q0 = i * kChunk;
     const int s = q0 / (2 * KC), h = (q0 % (2 * KC)) / KC, k0 = q0 % KC;
     const bool a_lo = (s == 2), b_lo = (s == 1);
+    // operands are read along whichever of their indices is contiguous in memory
+    const bool a_rows_fast = (a.sAm == 1), b_cols_fast = (a.sBn == 1);
     for (int e = tid; e < 128 * kChunk; e += kTcThreads) {
-      const int m = e / kChunk, t = e - m * kChunk;
+      int m, t;
+      if (a_rows_fast) {
+        t = e >> 7;
+        m = e & 127;
+      } else {
+        m = e / kChunk;
+        t = e - m * kChunk;
+      }
       float v = 0.f;
       if (m < a.rowsA) {
         const float2 z = A[(long)m * a.sAm + (long)(k0 + t) * a.sAk];
@@ -152,7 +161,14 @@ __global__ void __launch_bounds__(kTcThreads) tc_cgemm_kernel(const CgemmArgs a)
       *reinterpret_cast<__nv_bfloat16*>(sA[st] + core_off(m, t)) = a_lo ? lo : hi;
     }
     for (int e = tid; e < NR * kChunk; e += kTcThreads) {
-      const int j = e / kChunk, t = e - j * kChunk;
+      int j, t;
+      if (b_cols_fast) {
+        t = e / NR;
+        j = e - t * NR;
+      } else {
+        j = e / kChunk;
+        t = e - j * kChunk;
+      }
       const int n = (j < NC) ? j : j - NC;
       const float2 z = B[(long)(k0 + t) * a.sBk + (long)n * a.sBn];
       // [[Br Bi], [-Bi Br]]: first half of K pairs with Ar, second with Ai

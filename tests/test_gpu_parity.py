@@ -249,3 +249,27 @@ def test_device_pointers_through_torch():
         d = torch.empty((elf.N, elf.N), dtype=torch.complex64, device=dev)
         elf.get_spectrum(d)
         assert np.array_equal(d.cpu().numpy(), host)
+
+
+@pytest.mark.parametrize("name", ["small32", "w0", "w1"])
+@pytest.mark.parametrize("variant", [dict(fidelity=1), dict(omega_iso=0), dict(pupil_filter=0)])
+def test_option_variants_one_iteration(name, variant):
+    """Amplitude fidelity (Eqs. 4, 10, 17), anisotropic normaliser (Eq. 12 second case) and the
+    unfiltered pupil update: one iteration from the same developed state."""
+    c = case(name)
+    st = developed_state(name, **variant)
+    I = c["I"].astype(np.float64)
+    opt = O.Options(**variant)
+    ref, costs_ref, _ = O.iteration(st, I, c["geo"], opt)
+    with make_elf(c, **variant) as elf:
+        elf.set_measurements(c["I"])
+        a_gpu, _ = elf.get_weights()
+        load_state(elf, st)
+        elf.step(1)
+        out = elf.get_state()
+        costs = elf.get_costs()[-1]
+    a_ref = O.alpha_estimate(I, amplitude=(variant.get("fidelity", 0) == 1))
+    e = dict(alpha=abs(a_gpu - a_ref) / a_ref, psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
+             cost=float(np.max(np.abs(costs - np.asarray(costs_ref)) / np.asarray(costs_ref))))
+    print(name, variant, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["alpha"] < 1e-6 and e["psi"] < TOL_STATE and e["pupil"] < TOL_STATE and e["cost"] < TOL_FWD
