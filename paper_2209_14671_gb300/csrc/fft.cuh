@@ -158,19 +158,17 @@ struct FftTeam {
 };
 
 // Twiddle table of a team transform: tw[k1 * Q + l] = W_L^{l k1} (forward sign).
-// In-place transform of buf (padded layout) by one team.  Inputs outside
+// team_fft: in-place transform of buf (padded layout) by one team.  Inputs outside
 // [lo, lo + cnt) are taken as zero without being read.  Every lane of the warp
 // must call this (inactive lanes pass active = false).
+// team_fft_regs starts from registers instead: v[j] = x[lane + Q j], j < P (the
+// values pass 1 would read), and leaves the result in buf.
 template <int L, bool INV>
-__device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__ tw, int lane, bool active,
-                                         int lo = 0, int cnt = L) {
+__device__ __forceinline__ void team_fft_regs(float2* v, float2* buf, const float2* __restrict__ tw, int lane,
+                                              bool active) {
   using T = FftTeam<L>;
   constexpr int P = T::P, Q = T::Q;
-  float2 v[P];
   if (active) {
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-      v[j] = ((unsigned)(lane + Q * j - lo) < (unsigned)cnt) ? buf[lane + (Q + 1) * j] : make_float2(0.f, 0.f);
     Dft<P, INV>::run(v);
 #pragma unroll
     for (int k = 1; k < P; ++k) {
@@ -204,6 +202,19 @@ __device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__
     }
   }
   __syncwarp();
+}
+
+template <int L, bool INV>
+__device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__ tw, int lane, bool active,
+                                         int lo = 0, int cnt = L) {
+  constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
+  float2 v[P];
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      v[j] = ((unsigned)(lane + Q * j - lo) < (unsigned)cnt) ? buf[lane + (Q + 1) * j] : make_float2(0.f, 0.f);
+  }
+  team_fft_regs<L, INV>(v, buf, tw, lane, active);
 }
 
 }  // namespace elf

@@ -30,12 +30,17 @@ namespace cg = cooperative_groups;
 namespace elf {
 
 // Tile configuration per image side n: cluster size CS and threads per CTA NT.
-//   n = 256: 8 CTAs of 512 threads (~130 KB shared memory each, one per SM)
-//   n = 128: 4 CTAs of 256 threads (~64 KB), n = 64: 2 CTAs of 256 threads (~36 KB)
+// A CTA owns n/CS = 32 columns and transforms 34 (one halo column per side), so NT
+// holds at least 34 FFT teams and every column pass is a single round:
+//   n = 256: 8 CTAs of 544 threads (34 teams of 16 lanes; ~137 KB shared memory, one per SM)
+//   n = 128: 4 CTAs of 288 threads (36 teams of 8; ~64 KB), n = 64: 2 CTAs of 288 (~36 KB)
 template <int NL> struct TileCfg { static constexpr int CS = 1, NT = 256; };
-template <> struct TileCfg<64> { static constexpr int CS = 2, NT = 256; };
-template <> struct TileCfg<128> { static constexpr int CS = 4, NT = 256; };
-template <> struct TileCfg<256> { static constexpr int CS = 8, NT = 512; };
+template <> struct TileCfg<64> { static constexpr int CS = 2, NT = 288; };
+template <> struct TileCfg<128> { static constexpr int CS = 4, NT = 288; };
+template <> struct TileCfg<256> { static constexpr int CS = 8, NT = 544; };
+
+// largest power of two <= w (the warps that walk row strips in the stencil pass)
+__host__ __device__ constexpr int pow2_floor(int w) { return w >= 16 ? 16 : w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1; }
 
 template <int CS>
 __device__ __forceinline__ void cluster_barrier() {
@@ -61,7 +66,9 @@ struct OmegaOut {
   float wx, wy, phi;
 };
 
-template <int NL, int CS, int NT>
+// FID: 0 = intensity fidelity (Eq. 5), 1 = amplitude (Eq. 4); ISO: 1 = isotropic normaliser,
+// 0 = anisotropic (Eq. 12).  Compile-time, so the per-pixel loops carry no untaken branch work.
+template <int NL, int CS, int NT, int FID, int ISO>
 __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int NW = NT / 32;
   constexpr int TL = FftTeam<NL>::TL;
@@ -90,7 +97,15 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const int x0 = crank * CW;
   const size_t img = (size_t)led * NL * NL;
 
-  // prefetch this CTA's columns of I_n (16-byte cp.async chunks; overlaps stages A and B)
+  // twiddles (group 0) and this CTA's columns of I_n (group 1, overlapping stages A and B)
+  // arrive by cp.async in 16-byte chunks
+  {
+    const unsigned tbase = (unsigned)__cvta_generic_to_shared(tw);
+    for (int i = tid; i < NL / 2; i += NT)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tbase + 16u * i), "l"(a.tw + 2 * i)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   if (a.mode == 0) {
     constexpr int CH = CW / 4;  // 16-byte chunks per row
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(Itile);
@@ -110,7 +125,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  for (int i = tid; i < NL; i += NT) tw[i] = a.tw[i];
+  if (a.mode == 0) {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  } else {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  }
   cluster_barrier<CS>();  // every CTA of the cluster is running before any remote store
 
   const int2 org = a.origin[led];
@@ -124,17 +143,26 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     float2* row = A1 + (act ? lb : 0) * RP;
     const int y = a.Blo + b0 + (act ? lb : 0);
     const int py = FftTeam<NL>::pidx(y);
+    // crop x pupil straight into the registers of the transform's first pass (x = lane + TL j);
+    // every load is issued before the first product
+    constexpr int PL = FftTeam<NL>::P;
+    float2 v[PL];
     if (act) {
       const int xs = a.row_xs[y], cnt = a.row_cnt[y];
       const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
-      for (int x = lane; x < NL; x += TL) {
-        float2 v = make_float2(0.f, 0.f);
-        if ((unsigned)(x - xs) < (unsigned)cnt) v = cmul(a.pupil[y * NL + x], prow[x]);
-        row[FftTeam<NL>::pidx(x)] = v;
+      const float2* pp = a.pupil + (size_t)y * NL;
+      float2 pv[PL];
+#pragma unroll
+      for (int j = 0; j < PL; ++j) {
+        const int x = lane + TL * j;
+        const bool in = (unsigned)(x - xs) < (unsigned)cnt;
+        pv[j] = in ? pp[x] : make_float2(0.f, 0.f);
+        v[j] = in ? prow[x] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
     }
-    __syncwarp();
-    team_fft<NL, true>(row, tw, lane, act);
+    team_fft_regs<NL, true>(v, row, tw, lane, act);
     if (act) {
       for (int x = lane; x < NL; x += TL) {
         const float2 v = row[FftTeam<NL>::pidx(x)];
@@ -174,7 +202,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // residual r = |o|^2 - I (Eq. 5) or |o| - sqrt(max(I, 0)) (Eq. 4)
   auto resid = [&](float2 o, float meas) -> float {
     const float m2 = cabs2(o);
-    return (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
+    if constexpr (FID == 0) {
+      return m2 - meas;
+    } else {
+      return sqrtf(m2) - sqrtf(fmaxf(meas, 0.f));
+    }
   };
 
   // W = o * nabla^T omega (Eq. 11) or o / (2 max(|o|, eta)) * nabla^T omega (Eq. 10),
@@ -184,22 +216,25 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // normaliser are evaluated once per pixel, x-neighbours come by shuffle and the
   // halo columns are evaluated by the edge lanes.  The rows just outside the strip
   // are read before a block barrier, because their owners overwrite them with W.
-  float acc = 0.f;  // per-thread partial of at most NL/NW pixels; block sum in FP64
+  float acc = 0.f;  // per-thread partial of at most NL/SW pixels; block sum in FP64
   {
     static_assert(CW <= 32, "one warp spans the owned columns");
-    constexpr int RPW = NL / NW;  // rows per warp
+    constexpr int SW = pow2_floor(NW);  // strip warps; the others only take part in the barrier
+    constexpr int RPW = NL / SW;        // rows per strip
+    static_assert(RPW * SW == NL, "strips tile the rows");
     const float tau = a.tau, tau2 = fmaxf(a.tau * a.tau, 1e-36f), hit = (a.tau > 0.f) ? 0.5f / a.tau : 0.f;
     const bool on = wl < CW;
     const int cc = on ? wl : 0;
     const int c = cc + 1, x = x0 + cc;
     const bool has_left = x0 >= 1, has_right = x0 + CW < NL;
-    const int ybeg = warp * RPW, yend = ybeg + RPW;
+    const bool strip = warp < SW;
+    const int ybeg = strip ? warp * RPW : 0, yend = strip ? ybeg + RPW : 0;  // empty strip: no rows
     auto r_own = [&](int y) { return resid(load_o(y, c, x), Itile[y * CW + cc]); };
     auto r_left = [&](int y) { return resid(load_o(y, 0, x0 - 1), Ihalo[y]); };
     auto r_right = [&](int y) { return resid(load_o(y, CW + 1, x0 + CW), Ihalo[NL + y]); };
     auto huber2 = [&](float dx, float dy) -> OmegaOut {
       OmegaOut o;
-      if (a.iso) {
+      if constexpr (ISO != 0) {
         const float ss = dx * dx + dy * dy;
         const float inv = rsqrtf(fmaxf(ss, tau2));
         o.wx = dx * inv;
@@ -265,7 +300,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         if (y >= 1) w += wy_prev;
         acc += w0.phi;
         float f = w;
-        if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
+        if constexpr (FID != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
         // W times (-1)^(x+y) for the forward fftshift; o_cur already carries the inverse one
         OC[c * LD + FftTeam<NL>::pidx(y)] = cscale(o_cur, ((x + y) & 1) ? -f : f);
       }
@@ -361,7 +396,13 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT>, a);
+  const int var = (a.mode == 1) ? 1 : (a.fidelity ? 2 : 0) + (a.iso ? 1 : 0);
+  switch (var) {
+    case 0: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 0>, a);
+    case 1: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 1>, a);
+    case 2: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 1, 0>, a);
+    default: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 1, 1>, a);
+  }
 }
 
 template <int NL>
@@ -370,7 +411,10 @@ static cudaError_t prepare_tile_t(int rowsA) {
   static int configured = 0;  // largest dynamic shared memory size set so far
   const int smem = (int)tile_smem_bytes(NL, CS, rowsA);
   if (smem <= configured) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(tile_kernel<NL, CS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaSuccess;
+  for (auto k : {tile_kernel<NL, CS, NT, 0, 0>, tile_kernel<NL, CS, NT, 0, 1>, tile_kernel<NL, CS, NT, 1, 0>,
+                 tile_kernel<NL, CS, NT, 1, 1>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) configured = smem;
   return e;
 }
