@@ -158,13 +158,16 @@ struct FftTeam {
 };
 
 // Twiddle table of a team transform: tw[k1 * Q + l] = W_L^{l k1} (forward sign).
-// team_fft: in-place transform of buf (padded layout) by one team.  Inputs outside
-// [lo, lo + cnt) are taken as zero without being read.  Every lane of the warp
-// must call this (inactive lanes pass active = false).
-// team_fft_regs starts from registers instead: v[j] = x[lane + Q j], j < P (the
-// values pass 1 would read), and leaves the result in buf.
-template <int L, bool INV>
-__device__ __forceinline__ void team_fft_regs(float2* v, float2* buf, const float2* __restrict__ tw, int lane,
+//
+// The buffer of one transform holds element e at buf[e * S] (S = 1: contiguous; a
+// larger S walks a column of a row-major array), e < PADDED; data index i lives at
+// e = pidx(i).  Every lane of the warp must call these (inactive lanes pass
+// active = false).
+//
+// team_fft_core: v[j] = x[lane + Q j] (j < P) on entry, the values pass 1 reads;
+// on return v[m * Q + k2] = X[k1 + P k2] with k1 = lane + Q m.  buf is scratch.
+template <int L, bool INV, int S = 1>
+__device__ __forceinline__ void team_fft_core(float2* v, float2* buf, const float2* __restrict__ tw, int lane,
                                               bool active) {
   using T = FftTeam<L>;
   constexpr int P = T::P, Q = T::Q;
@@ -180,7 +183,7 @@ __device__ __forceinline__ void team_fft_regs(float2* v, float2* buf, const floa
   __syncwarp();
   if (active) {
 #pragma unroll
-    for (int k = 0; k < P; ++k) buf[k * (Q + 1) + lane] = v[k];
+    for (int k = 0; k < P; ++k) buf[(k * (Q + 1) + lane) * S] = v[k];
   }
   __syncwarp();
   if (active) {
@@ -188,23 +191,34 @@ __device__ __forceinline__ void team_fft_regs(float2* v, float2* buf, const floa
     for (int m = 0; m < P / Q; ++m) {
       const int k1 = lane + Q * m;
 #pragma unroll
-      for (int l = 0; l < Q; ++l) v[m * Q + l] = buf[k1 * (Q + 1) + l];
+      for (int l = 0; l < Q; ++l) v[m * Q + l] = buf[(k1 * (Q + 1) + l) * S];
       Dft<Q, INV>::run(v + m * Q);
-    }
-  }
-  __syncwarp();
-  if (active) {
-#pragma unroll
-    for (int m = 0; m < P / Q; ++m) {
-      const int k1 = lane + Q * m;
-#pragma unroll
-      for (int k2 = 0; k2 < Q; ++k2) buf[T::pidx(k1 + P * k2)] = v[m * Q + k2];
     }
   }
   __syncwarp();
 }
 
-template <int L, bool INV>
+// team_fft_regs: team_fft_core, then X in natural order into buf (element pidx(k)).
+template <int L, bool INV, int S = 1>
+__device__ __forceinline__ void team_fft_regs(float2* v, float2* buf, const float2* __restrict__ tw, int lane,
+                                              bool active) {
+  using T = FftTeam<L>;
+  constexpr int P = T::P, Q = T::Q;
+  team_fft_core<L, INV, S>(v, buf, tw, lane, active);
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P / Q; ++m) {
+      const int k1 = lane + Q * m;
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) buf[T::pidx(k1 + P * k2) * S] = v[m * Q + k2];
+    }
+  }
+  __syncwarp();
+}
+
+// team_fft: in-place transform of buf.  Inputs outside [lo, lo + cnt) are taken as
+// zero without being read.
+template <int L, bool INV, int S = 1>
 __device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__ tw, int lane, bool active,
                                          int lo = 0, int cnt = L) {
   constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
@@ -212,9 +226,10 @@ __device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__
   if (active) {
 #pragma unroll
     for (int j = 0; j < P; ++j)
-      v[j] = ((unsigned)(lane + Q * j - lo) < (unsigned)cnt) ? buf[lane + (Q + 1) * j] : make_float2(0.f, 0.f);
+      v[j] = ((unsigned)(lane + Q * j - lo) < (unsigned)cnt) ? buf[(lane + (Q + 1) * j) * S]
+                                                             : make_float2(0.f, 0.f);
   }
-  team_fft_regs<L, INV>(v, buf, tw, lane, active);
+  team_fft_regs<L, INV, S>(v, buf, tw, lane, active);
 }
 
 }  // namespace elf

@@ -9,6 +9,7 @@
 //   init kernels     the initial state of elf_set_measurements
 #include "fft.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace elf {
 
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   __shared__ float s_a[HA][HA + 1];
   __shared__ float s_p[HA][HA + 1];
   __shared__ float s_w[6][HW][HW + 1];
-  __shared__ double red[8];
+  __shared__ float red[4 * 8];
   const int N = a.N;
   const int tx0 = blockIdx.x * HT, ty0 = blockIdx.y * HT;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -147,12 +148,13 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
     a.q[(size_t)y * N + x] = cscale(q, sg);
   }
   (void)tid;
-  const double sa = block_sum_double((double)ca, red);
-  const double sp = block_sum_double((double)cp, red);
+  const float part[2] = {ca, cp};
+  double sum[2];
+  block_sum_ff<2>(part, red, sum);
   if (tid == 0) {
     const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    a.costpart[2 * b] = sa;
-    a.costpart[2 * b + 1] = sp;
+    a.costpart[2 * b] = sum[0];
+    a.costpart[2 * b + 1] = sum[1];
   }
 }
 
@@ -324,19 +326,21 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s) {
 // an iteration (advance) it also increments t, advances the running powers
 // gp = (gamma1^(t+1), gamma2^(t+1)) and stores the bias corrections 1/(1 - gp) of
 // Eq. 19 for the next iteration.
-__global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int nfid, const double* hp, int nh,
-                                                          double* ring, int* t_dev, double* out3, int advance,
-                                                          float* bc, double* gp, double g1, double g2) {
-  __shared__ double red[8];
+__global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, int nfid, const double* hp, int nh,
+                                                           double* ring, int* t_dev, double* out3, int advance,
+                                                           float* bc, double* gp, double g1, double g2) {
+  // per-thread sums in FP64 over a fixed stride, then one block sum of (hi, lo) pairs
+  __shared__ float red[2 * 3 * 32];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int i = threadIdx.x; i < nfid; i += 256) s0 += fid[i];
-  for (int i = threadIdx.x; i < nh; i += 256) {
+  for (int i = threadIdx.x; i < nfid; i += blockDim.x) s0 += fid[i];
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     s1 += hp[2 * i];
     s2 += hp[2 * i + 1];
   }
-  const double a0 = block_sum_double(s0, red);
-  const double a1 = block_sum_double(s1, red);
-  const double a2 = block_sum_double(s2, red);
+  const FF part[3] = {ff_from_double(s0), ff_from_double(s1), ff_from_double(s2)};
+  double sum[3];
+  block_sum_ff<3>(part, red, sum);
+  const double a0 = sum[0], a1 = sum[1], a2 = sum[2];
   if (threadIdx.x == 0) {
     if (out3) {
       out3[0] = a0;
@@ -378,7 +382,7 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring, int* t_dev,
                                double* out3, int advance, float* bc, double* gp, double g1, double g2,
                                cudaStream_t s) {
-  cost_reduce_kernel<<<1, 256, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance, bc, gp, g1, g2);
+  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance, bc, gp, g1, g2);
   return cudaGetLastError();
 }
 

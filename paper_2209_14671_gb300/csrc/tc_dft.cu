@@ -29,6 +29,7 @@
 
 #include "fft.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace elf {
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(512) tc_stencil_kernel(const TcArgs a) {
   float* R = s_f;                 // n x n residual
   float* WX = R + n * n;          // n x n omega_x
   float* WY = WX + n * n;         // n x n omega_y
-  __shared__ double red[16];
+  __shared__ float red[2 * 16];
   const int b = blockIdx.x, tid = threadIdx.x;
   const float2* O = a.O + (size_t)b * n * n;
   const float* I = a.meas + (size_t)b * n * n;
@@ -334,16 +335,10 @@ __global__ void __launch_bounds__(512) tc_stencil_kernel(const TcArgs a) {
     if ((x + y) & 1) f = -f;
     a.Wt[(size_t)b * n * n + p] = cscale(o, f);
   }
-  double d = (double)acc;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
-  if ((tid & 31) == 0) red[tid >> 5] = d;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    a.costpart[b] = t;
-  }
+  const float part[1] = {acc};
+  double sum[1];
+  block_sum_ff<1>(part, red, sum);
+  if (tid == 0) a.costpart[b] = sum[0];
 }
 
 // G on the support (compact order) from the band block G~ (64 x 64), times u^-2 n^-2.

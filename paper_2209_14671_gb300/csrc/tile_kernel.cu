@@ -24,6 +24,7 @@
 
 #include "fft.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -38,6 +39,14 @@ template <int NL> struct TileCfg { static constexpr int CS = 1, NT = 256; };
 template <> struct TileCfg<64> { static constexpr int CS = 2, NT = 288; };
 template <> struct TileCfg<128> { static constexpr int CS = 4, NT = 288; };
 template <> struct TileCfg<256> { static constexpr int CS = 8, NT = 544; };
+
+// Row pitch (in float2) of the per-CTA column buffer: at least the 34 (or n + 2) owned and
+// halo columns, and chosen so that the column transforms' strided accesses by the teams
+// of one half-warp fall in distinct banks (odd for 16-lane teams, 2 mod 16 for 8-lane
+// teams, 4 mod 16 for 4-lane teams).
+__host__ __device__ constexpr int oc_pitch(int n) {
+  return n == 256 ? 35 : n == 128 ? 34 : n == 64 ? 34 : n == 32 ? 36 : 20;
+}
 
 // largest power of two <= w (the warps that walk row strips in the stencil pass)
 __host__ __device__ constexpr int pow2_floor(int w) { return w >= 16 ? 16 : w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1; }
@@ -76,16 +85,17 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int CW = NL / CS;     // owned columns
   constexpr int WC = CW + 2;      // with one halo column per side
   constexpr int RP = FftTeam<NL>::PADDED;  // FFT buffer length (padded layout)
-  constexpr int LD = RP + 1;      // column pitch of OC (odd: conflict-free across columns)
+  constexpr int PO = oc_pitch(NL);          // row pitch of OC (conflict-free column transforms)
+  static_assert(PO >= WC, "OC rows hold the owned and halo columns");
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Itile = reinterpret_cast<float*>(smem_raw);      // NL x CW measured intensities (row-major)
   float* Ihalo = Itile + NL * CW;                          // 2 x NL: the halo columns x0-1, x0+CW
   float2* tw = reinterpret_cast<float2*>(Ihalo + 2 * NL);
   float2* A1 = tw + NL;                                   // rowsA band rows of pitch RP
-  float2* OC = A1 + a.rowsA * RP;                         // WC columns of pitch LD
-  float* Hx = reinterpret_cast<float*>(OC + WC * LD);     // 2 x NL: r at x0+CW, omega_x at x0-1
-  double* red = reinterpret_cast<double*>(Hx + 2 * NL);
+  float2* OC = A1 + a.rowsA * RP;                         // RP rows of PO: row pidx(y), column 1 + x - x0
+  float* Hx = reinterpret_cast<float*>(OC + RP * PO);     // 2 x NL: r at x0+CW, omega_x at x0-1
+  float* red = Hx + 2 * NL;                                 // 2 floats per warp
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, wl = tid & 31;
@@ -162,15 +172,23 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
 #pragma unroll
       for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
     }
-    team_fft_regs<NL, true>(v, row, tw, lane, act);
+    team_fft_core<NL, true>(v, row, tw, lane, act);
+    // the transform leaves X[k1 + P k2] in v[m Q + k2] (k1 = lane + Q m): a team's lanes hold
+    // consecutive x, so each store below writes a contiguous run of the owner's row py
     if (act) {
-      for (int x = lane; x < NL; x += TL) {
-        const float2 v = row[FftTeam<NL>::pidx(x)];
-        const int own = x / CW, c = x - own * CW + 1;
-        remote<CS>(OC, own)[c * LD + py] = v;
-        if (CS > 1) {
-          if (c == CW && own + 1 < CS) remote<CS>(OC, own + 1)[0 * LD + py] = v;   // left halo of the next CTA
-          if (c == 1 && own > 0) remote<CS>(OC, own - 1)[(CW + 1) * LD + py] = v;  // right halo of the previous
+      constexpr int Q = FftTeam<NL>::Q;
+#pragma unroll
+      for (int m = 0; m < PL / Q; ++m) {
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int x = lane + Q * m + PL * k2;
+          const float2 val = v[m * Q + k2];
+          const int own = x / CW, c = x - own * CW + 1;
+          remote<CS>(OC, own)[py * PO + c] = val;
+          if (CS > 1) {
+            if (c == CW && own + 1 < CS) remote<CS>(OC, own + 1)[py * PO] = val;        // left halo of the next CTA
+            if (c == 1 && own > 0) remote<CS>(OC, own - 1)[py * PO + CW + 1] = val;     // right halo of the previous
+          }
         }
       }
     }
@@ -183,14 +201,14 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     const int lc = base + team;
     const int x = x0 - 1 + lc;
     const bool act = (lc < WC) && x >= 0 && x < NL;
-    team_fft<NL, true>(OC + (act ? lc : 0) * LD, tw, lane, act, a.Blo, a.nb);
+    team_fft<NL, true, PO>(OC + (act ? lc : 0), tw, lane, act, a.Blo, a.nb);
   }
   if (a.mode == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
   // o = (-1)^(x+y) scale * IDFT (register values; the raw transform stays in OC)
   auto load_o = [&](int y, int c, int x) -> float2 {
-    const float2 o = OC[c * LD + FftTeam<NL>::pidx(y)];
+    const float2 o = OC[FftTeam<NL>::pidx(y) * PO + c];
     const float sg = ((x + y) & 1) ? -a.scale : a.scale;
     return make_float2(o.x * sg, o.y * sg);
   };
@@ -302,7 +320,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         float f = w;
         if constexpr (FID != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
         // W times (-1)^(x+y) for the forward fftshift; o_cur already carries the inverse one
-        OC[c * LD + FftTeam<NL>::pidx(y)] = cscale(o_cur, ((x + y) & 1) ? -f : f);
+        OC[FftTeam<NL>::pidx(y) * PO + c] = cscale(o_cur, ((x + y) & 1) ? -f : f);
       }
       wy_prev = w0.wy;
       o_cur = o_nxt;
@@ -311,44 +329,54 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       i_nxt = i_nn;
     }
   }
-  // block reduction of the cost partials in FP64 (fixed order)
-  double accd = (double)acc;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
-  if (wl == 0) red[warp] = accd;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < NW; ++i) s += red[i];
-    a.costpart[led * CS + crank] = s;
+  // block sum of the cost partials (fixed order, FP64-level accuracy)
+  {
+    const float part[1] = {acc};
+    double sum[1];
+    block_sum_ff<1>(part, red, sum);
+    if (tid == 0) a.costpart[led * CS + crank] = sum[0];
   }
 
   // forward column transforms of the owned columns, then push the band rows to their owners
   for (int base = 0; base < CW; base += NTEAM) {
     const int cw = base + team;
     const bool act = cw < CW;
-    team_fft<NL, false>(OC + (act ? cw + 1 : 1) * LD, tw, lane, act);
+    team_fft<NL, false, PO>(OC + (act ? cw + 1 : 1), tw, lane, act);
   }
   __syncthreads();
   for (int b = warp; b < a.nb; b += NW) {
     const int own = b / a.rowsA, lb = b - own * a.rowsA;
     float2* dst = remote<CS>(A1, own) + lb * RP;
     const int py = FftTeam<NL>::pidx(a.Blo + b);
-    for (int cc = wl; cc < CW; cc += 32) dst[FftTeam<NL>::pidx(x0 + cc)] = OC[(cc + 1) * LD + py];
+    for (int cc = wl; cc < CW; cc += 32) dst[FftTeam<NL>::pidx(x0 + cc)] = OC[py * PO + cc + 1];
   }
   cluster_barrier<CS>();
 
-  // ---- C: forward row transforms of this CTA's band rows; keep the support
+  // ---- C: forward row transforms of this CTA's band rows; the support pixels go
+  // from the transform's registers straight to G
   for (int base = 0; base < a.rowsA; base += NTEAM) {
     const int lb = base + team;
     const bool act = lb < nrows;
     float2* row = A1 + (act ? lb : 0) * RP;
-    team_fft<NL, false>(row, tw, lane, act);
+    constexpr int PL = FftTeam<NL>::P, Q = FftTeam<NL>::Q;
+    float2 v[PL];
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < PL; ++j) v[j] = row[lane + (Q + 1) * j];
+    }
+    team_fft_core<NL, false>(v, row, tw, lane, act);
     if (act) {
       const int ky = a.Blo + b0 + lb;
       const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
       float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
-      for (int i = lane; i < cnt; i += TL) dst[i] = cscale(row[FftTeam<NL>::pidx(xs + i)], a.scale);
+#pragma unroll
+      for (int m = 0; m < PL / Q; ++m) {
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int d = lane + Q * m + PL * k2 - xs;
+          if ((unsigned)d < (unsigned)cnt) dst[d] = cscale(v[m * Q + k2], a.scale);
+        }
+      }
     }
   }
 }
@@ -373,9 +401,9 @@ static int tile_threads(int n) {
 
 size_t tile_smem_bytes(int n, int cs, int rowsA) {
   const size_t rp = fft_padded_length(n);
-  const size_t cw = n / cs, wc = cw + 2, ld = rp + 1;
-  return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + wc * ld) + 4 * 2 * (size_t)n +
-         8 * (size_t)(tile_threads(n) / 32);
+  const size_t cw = n / cs;
+  return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
+         4 * 2 * (size_t)n + 8 * (size_t)(tile_threads(n) / 32);
 }
 
 template <int NL>
