@@ -78,6 +78,7 @@ struct elf_handle_s {
   // scratch
   float2 *G = nullptr, *ot = nullptr, *q = nullptr, *small = nullptr, *part = nullptr;
   float2 *psi_eval = nullptr, *pupil_eval = nullptr, *g_psi = nullptr, *g_p = nullptr, *pupil_unit = nullptr;
+  float2* cost_ff = nullptr;  // per-warp (hi, lo) fidelity cost partials of the tile kernel
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
          *out3 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
@@ -177,7 +178,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ta.row_off = h->row_off;
   ta.tw = h->tw_n;
   ta.G = h->G;
-  ta.costpart = h->cost_fid;
+  ta.cost_ff = h->cost_ff;
   ta.I_out = nullptr;
   ta.N = h->N;
   ta.K = h->K;
@@ -301,7 +302,9 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 1);
   }
   ELF_MARK(s0, ELF_STAGE_COST, 0);
-  ELF_CK(launch_cost_reduce(h->cost_fid, h->opt.tile_dft ? h->K : h->K * h->cs, h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
+  const bool tc = h->opt.tile_dft != 0;
+  ELF_CK(launch_cost_reduce(h->cost_fid, tc ? h->K : 0, h->cost_ff, tc ? 0 : h->K * h->cs * tile_warps(h->n),
+                            h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
                             h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, h->bc, h->gp,
                             h->opt.gamma1, h->opt.gamma2, s0));
   ELF_MARK(s0, ELF_STAGE_COST, 1);
@@ -550,7 +553,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->g_psi, A))) return rc;
   if ((rc = dalloc(h, &h->g_p, B))) return rc;
   if ((rc = dalloc(h, &h->pupil_unit, B))) return rc;
-  if ((rc = dalloc(h, &h->cost_fid, (size_t)K * h->cs))) return rc;
+  if ((rc = dalloc(h, &h->cost_fid, (size_t)K))) return rc;
+  if ((rc = dalloc(h, &h->cost_ff, (size_t)K * h->cs * tile_warps(n)))) return rc;
   if ((rc = dalloc(h, &h->cost_h, (size_t)2 * h->hblocks))) return rc;
   if ((rc = dalloc(h, &h->ring, (size_t)3 * kCostRing))) return rc;
   if ((rc = dalloc(h, &h->weights, 2))) return rc;
@@ -849,7 +853,7 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   ta.row_off = h->row_off;
   ta.tw = h->tw_n;
   ta.I_out = dst;
-  ta.costpart = h->cost_fid;
+  ta.cost_ff = h->cost_ff;
   ta.N = h->N;
   ta.K = h->K;
   ta.S = h->S;

@@ -20,7 +20,7 @@ struct TileArgs {
   const int* row_off;     // n: compact index of the first support pixel of each row
   const float2* tw;       // n team twiddles tw[k1 * Q + l] = e^{-2 pi i l k1 / n}
   float2* G;              // K x S tile gradients on the support (gradient mode)
-  double* costpart;       // K x CS fidelity cost partials
+  float2* cost_ff;        // K x CS x warps fidelity cost partials, (hi, lo) float pairs
   float* I_out;           // K x n x n predicted intensities (simulate mode)
   int N, K, S, Blo, nb, rowsA;
   float scale;            // 1 / (u^2 n^2)
@@ -29,6 +29,7 @@ struct TileArgs {
   int mode;               // 0 = gradient, 1 = simulate |o|^2
 };
 int tile_cluster_size(int n);
+int tile_warps(int n);                        // warps per CTA of the tile kernel
 size_t tile_smem_bytes(int n, int cs, int rowsA);
 cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
 cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
@@ -120,7 +121,8 @@ cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s);
 cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
-cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring,
+cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
+                               double* ring,
                                int* t_dev, double* out3, int advance, float* bc, double* gp, double g1,
                                double g2, cudaStream_t s);
 cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);

@@ -76,9 +76,11 @@ std::string make_key(const elf_problem& p, const elf_options& o) {
 size_t estimate_bytes(const elf_problem& p) {
   const size_t n = p.n_lowres, N = (size_t)p.n_lowres * p.upsample, K = p.n_led;
   const size_t A = N * N, B = n * n, S = B;  // the support is at most the whole pupil grid
-  // Psi-sized: 6 complex + 2 real; per LED: I and G plus the Eq. 18 partials; pupil-sized: 8 complex
-  // + 3 real/int; 1 MB for the remaining tables, twiddles and reductions
-  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + 8 * B * 8 + 4 * B * 3 + (1u << 20);
+  // Psi-sized: 6 complex + 2 real; per LED: I and G plus the Eq. 18 partials and the tile kernel's
+  // per-warp cost pairs; pupil-sized: 8 complex + 3 real/int; 1 MB for the remaining tables,
+  // twiddles and reductions
+  const size_t cost_pairs = 8 * (size_t)elf::tile_cluster_size((int)n) * (size_t)elf::tile_warps((int)n);
+  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + (1u << 20);
 }
 
 }  // namespace

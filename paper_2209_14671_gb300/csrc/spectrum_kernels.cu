@@ -326,18 +326,25 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s) {
 // an iteration (advance) it also increments t, advances the running powers
 // gp = (gamma1^(t+1), gamma2^(t+1)) and stores the bias corrections 1/(1 - gp) of
 // Eq. 19 for the next iteration.
-__global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, int nfid, const double* hp, int nh,
-                                                           double* ring, int* t_dev, double* out3, int advance,
-                                                           float* bc, double* gp, double g1, double g2) {
-  // per-thread sums in FP64 over a fixed stride, then one block sum of (hi, lo) pairs
+__global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, int nfid, const float2* fidff, int nff,
+                                                           const double* hp, int nh, double* ring, int* t_dev,
+                                                           double* out3, int advance, float* bc, double* gp,
+                                                           double g1, double g2) {
+  // per-thread sums over a fixed stride (FP64 partials in FP64, (hi, lo) pairs as pairs),
+  // then one block sum of (hi, lo) pairs
   __shared__ float red[2 * 3 * 32];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nfid; i += blockDim.x) s0 += fid[i];
+  FF f0 = ff_from_double(s0);
+  for (int i = threadIdx.x; i < nff; i += blockDim.x) {
+    const float2 p = fidff[i];
+    f0 = ff_add(f0, FF{p.x, p.y});
+  }
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     s1 += hp[2 * i];
     s2 += hp[2 * i + 1];
   }
-  const FF part[3] = {ff_from_double(s0), ff_from_double(s1), ff_from_double(s2)};
+  const FF part[3] = {f0, ff_from_double(s1), ff_from_double(s2)};
   double sum[3];
   block_sum_ff<3>(part, red, sum);
   const double a0 = sum[0], a1 = sum[1], a2 = sum[2];
@@ -379,10 +386,11 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_cost_reduce(const double* fid, int nfid, const double* hp, int nh, double* ring, int* t_dev,
-                               double* out3, int advance, float* bc, double* gp, double g1, double g2,
-                               cudaStream_t s) {
-  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, hp, nh, ring, t_dev, out3, advance, bc, gp, g1, g2);
+cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
+                               double* ring, int* t_dev, double* out3, int advance, float* bc, double* gp,
+                               double g1, double g2, cudaStream_t s) {
+  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out3, advance, bc, gp, g1,
+                                        g2);
   return cudaGetLastError();
 }
 

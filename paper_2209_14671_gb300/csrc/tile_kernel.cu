@@ -3,21 +3,25 @@
 //
 // One LED = one thread-block cluster of CS CTAs.  The n x n tile never leaves
 // on-chip memory:
-//   0  each CTA starts an asynchronous copy (cp.async) of its columns of I_n;
+//   0  each CTA starts asynchronous copies (cp.async) of the twiddles and of its
+//      columns of I_n, and arrives at the cluster barrier it waits on in stage A;
 //   A  each CTA inverse-transforms its share of the support band rows
-//      (crop x pupil, zero outside the support) and pushes every value with a
-//      distributed-shared-memory store into the CTA owning that column (and into
-//      the neighbour that keeps it as a halo column): remote stores only, no
-//      remote loads on the critical path;
+//      (crop x pupil, zero outside the support, loaded straight into the
+//      transform's registers) and pushes the results from registers with
+//      distributed-shared-memory stores into the rows of the CTA owning each
+//      column (and of the neighbour that keeps it as a halo column): contiguous
+//      remote stores only, no remote loads;
 //   B  each CTA inverse-transforms the full columns it owns (n/CS of them, plus
 //      one halo column on each side), giving o_n on those columns;
-//      then r = |o|^2 - I (coalesced reads of I), the forward-difference
-//      gradient, the smoothed normaliser omega and W = o * nabla^T omega on the
-//      owned columns, with the per-pixel cost accumulated in FP64;
+//      then r = |o|^2 - I, the forward-difference gradient, the smoothed
+//      normaliser omega and W = o * nabla^T omega on the owned columns, with the
+//      per-pixel cost summed per warp as an unevaluated (hi, lo) float pair;
 //      then the forward column transforms of W, whose band rows are pushed to
 //      the CTAs owning those rows;
-//   C  each CTA forward-transforms its band rows, keeping the support pixels
-//      only (G_n).
+//   C  each CTA forward-transforms its band rows and writes the support pixels
+//      (G_n) from the transform's registers.
+// The column buffer OC is row-major (row pidx(y), one column per owned or halo x)
+// with a pitch that keeps the strided column transforms free of bank conflicts.
 // The (-1)^(x+y) factors realise ifftshift/fftshift for even n; the scale
 // 1/(u^2 n^2) is applied to o and to G.
 #include <cooperative_groups.h>
@@ -60,6 +64,17 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
+// The two halves of a cluster barrier (no memory ordering: used only to know that every CTA
+// of the cluster is running); every thread of every CTA executes both.
+template <int CS>
+__device__ __forceinline__ void cluster_arrive() {
+  if constexpr (CS > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+template <int CS>
+__device__ __forceinline__ void cluster_wait() {
+  if constexpr (CS > 1) asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+}
+
 template <int CS, typename T>
 __device__ __forceinline__ T* remote(T* p, int rank) {
   if constexpr (CS > 1) {
@@ -95,7 +110,6 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   float2* A1 = tw + NL;                                   // rowsA band rows of pitch RP
   float2* OC = A1 + a.rowsA * RP;                         // RP rows of PO: row pidx(y), column 1 + x - x0
   float* Hx = reinterpret_cast<float*>(OC + RP * PO);     // 2 x NL: r at x0+CW, omega_x at x0-1
-  float* red = Hx + 2 * NL;                                 // 2 floats per warp
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, wl = tid & 31;
@@ -135,12 +149,10 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  if (a.mode == 0) {
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-  } else {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  }
-  cluster_barrier<CS>();  // every CTA of the cluster is running before any remote store
+  // Every CTA of the cluster must be running before the first remote store: arrive now, wait
+  // just before the stage A pushes, so that the barrier's latency overlaps the crop loads and
+  // the first transforms.
+  cluster_arrive<CS>();
 
   const int2 org = a.origin[led];
   const int b0 = crank * a.rowsA;
@@ -172,7 +184,16 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
 #pragma unroll
       for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
     }
+    if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
+      if (a.mode == 0) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      __syncthreads();
+    }
     team_fft_core<NL, true>(v, row, tw, lane, act);
+    if (base == 0) cluster_wait<CS>();
     // the transform leaves X[k1 + P k2] in v[m Q + k2] (k1 = lane + Q m): a team's lanes hold
     // consecutive x, so each store below writes a contiguous run of the owner's row py
     if (act) {
@@ -192,6 +213,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         }
       }
     }
+  }
+  if (a.rowsA <= 0) {  // no band rows (not produced by the host): still complete both waits
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    cluster_wait<CS>();
   }
   cluster_barrier<CS>();
 
@@ -329,13 +355,12 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       i_nxt = i_nn;
     }
   }
-  // block sum of the cost partials (fixed order, FP64-level accuracy)
+  // the warp's cost pair, summed in a fixed order with the other warps' by the cost reduction
   {
-    const float part[1] = {acc};
-    double sum[1];
-    block_sum_ff<1>(part, red, sum);
-    if (tid == 0) a.costpart[led * CS + crank] = sum[0];
+    const FF wsum = warp_sum_ff(FF{acc, 0.f});
+    if (wl == 0) a.cost_ff[((size_t)led * CS + crank) * NW + warp] = make_float2(wsum.hi, wsum.lo);
   }
+  __syncthreads();  // W is complete in every column before the column transforms read it
 
   // forward column transforms of the owned columns, then push the band rows to their owners
   for (int base = 0; base < CW; base += NTEAM) {
@@ -403,8 +428,10 @@ size_t tile_smem_bytes(int n, int cs, int rowsA) {
   const size_t rp = fft_padded_length(n);
   const size_t cw = n / cs;
   return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
-         4 * 2 * (size_t)n + 8 * (size_t)(tile_threads(n) / 32);
+         4 * 2 * (size_t)n;
 }
+
+int tile_warps(int n) { return tile_threads(n) / 32; }
 
 template <int NL>
 static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
