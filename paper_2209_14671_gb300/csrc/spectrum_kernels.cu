@@ -217,16 +217,34 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
     }
   }
   __syncthreads();
+  // covering LEDs in ascending list order; the loads of four list entries are issued before
+  // their products are added (same additions in the same order as one entry at a time)
   float2 acc = make_float2(0.f, 0.f);
-  for (int i = 0; i < cnt; ++i) {
-    const int2 o = s_org[i];
-    const int jy = y - o.x, jx = x - o.y;
-    if ((unsigned)jy >= (unsigned)a.n) continue;
-    const int d = jx - s_rows[jy];
-    if ((unsigned)d >= (unsigned)s_rows[a.n + jy]) continue;
-    const float2 p = a.pupil[jy * a.n + jx];
-    const float2 gt = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
-    acc = cadd(acc, cconjmul(p, gt));
+  constexpr int U = 4;
+  for (int i0 = 0; i0 < cnt; i0 += U) {
+    float2 p[U], gt[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u;
+      ok[u] = false;
+      p[u] = gt[u] = make_float2(0.f, 0.f);
+      if (i < cnt) {
+        const int2 o = s_org[i];
+        const int jy = y - o.x, jx = x - o.y;
+        if ((unsigned)jy < (unsigned)a.n) {
+          const int d = jx - s_rows[jy];
+          if ((unsigned)d < (unsigned)s_rows[a.n + jy]) {
+            ok[u] = true;
+            p[u] = a.pupil[jy * a.n + jx];
+            gt[u] = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) acc = cadd(acc, cconjmul(p[u], gt[u]));
   }
   g = cadd(g, acc);
   if (a.mode == 1) {
@@ -263,11 +281,23 @@ __global__ void __launch_bounds__(256) pupil_partial_kernel(const PupilArgs a) {
   const int kc = (a.K + a.Q - 1) / a.Q;
   const int k0 = q * kc, k1 = min(a.K, k0 + kc);
   const int jy = a.sup_y[s], jx = a.sup_x[s];
+  // LEDs in ascending order; four at a time have their loads in flight together
   float2 acc = make_float2(0.f, 0.f);
-  for (int k = k0; k < k1; ++k) {
-    const int2 o = a.origin[k];
-    const float2 ps = a.psi[(size_t)(o.x + jy) * a.N + o.y + jx];
-    acc = cadd(acc, cconjmul(ps, a.G[(size_t)k * a.S + s]));
+  constexpr int U = 4;
+  for (int k = k0; k < k1; k += U) {
+    float2 ps[U], gt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ps[u] = gt[u] = make_float2(0.f, 0.f);
+      if (k + u < k1) {
+        const int2 o = a.origin[k + u];
+        ps[u] = a.psi[(size_t)(o.x + jy) * a.N + o.y + jx];
+        gt[u] = a.G[(size_t)(k + u) * a.S + s];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k + u < k1) acc = cadd(acc, cconjmul(ps[u], gt[u]));
   }
   a.part[(size_t)q * a.S + s] = acc;
 }
@@ -278,8 +308,18 @@ __global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
   if (j >= n * n) return;
   const int sidx = a.sidx_map[j];
   float2 g = make_float2(0.f, 0.f);
-  if (sidx >= 0)
-    for (int q = 0; q < a.Q; ++q) g = cadd(g, a.part[(size_t)q * a.S + sidx]);
+  if (sidx >= 0) {
+    constexpr int U = 8;  // loads of eight chunks in flight, added in chunk order
+    for (int q0 = 0; q0 < a.Q; q0 += U) {
+      float2 pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        pv[u] = (q0 + u < a.Q) ? a.part[(size_t)(q0 + u) * a.S + sidx] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q0 + u < a.Q) g = cadd(g, pv[u]);
+    }
+  }
   if (a.mode == 1) {
     a.g_out[j] = g;
     return;
@@ -336,9 +376,17 @@ __global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, in
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = threadIdx.x; i < nfid; i += blockDim.x) s0 += fid[i];
   FF f0 = ff_from_double(s0);
-  for (int i = threadIdx.x; i < nff; i += blockDim.x) {
-    const float2 p = fidff[i];
-    f0 = ff_add(f0, FF{p.x, p.y});
+  constexpr int U = 8;  // eight loads in flight, added in index order
+  for (int i0 = threadIdx.x; i0 < nff; i0 += U * blockDim.x) {
+    float2 pv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      pv[u] = (i < nff) ? fidff[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * (int)blockDim.x < nff) f0 = ff_add(f0, FF{pv[u].x, pv[u].y});
   }
   for (int i = threadIdx.x; i < nh; i += blockDim.x) {
     s1 += hp[2 * i];

@@ -232,15 +232,16 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   if (a.mode == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
-  // o = (-1)^(x+y) scale * IDFT (register values; the raw transform stays in OC)
-  auto load_o = [&](int y, int c, int x) -> float2 {
+  // o = (-1)^(x+y) scale * IDFT.  The stencil only needs |o| and W = o w times the same
+  // (-1)^(x+y) again (the forward shift), so the sign is never applied: o~ = scale * IDFT
+  // gives |o~| = |o| and (-1)^(x+y) o w = o~ w.
+  auto load_o = [&](int y, int c) -> float2 {
     const float2 o = OC[FftTeam<NL>::pidx(y) * PO + c];
-    const float sg = ((x + y) & 1) ? -a.scale : a.scale;
-    return make_float2(o.x * sg, o.y * sg);
+    return make_float2(o.x * a.scale, o.y * a.scale);
   };
   if (a.mode == 1) {  // forward model only: |o|^2 on the owned columns
     for (int y = warp; y < NL; y += NW)
-      for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1, x0 + cc));
+      for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1));
     return;  // no remote access after the last cluster barrier
   }
   // residual r = |o|^2 - I (Eq. 5) or |o| - sqrt(max(I, 0)) (Eq. 4)
@@ -273,9 +274,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     const bool has_left = x0 >= 1, has_right = x0 + CW < NL;
     const bool strip = warp < SW;
     const int ybeg = strip ? warp * RPW : 0, yend = strip ? ybeg + RPW : 0;  // empty strip: no rows
-    auto r_own = [&](int y) { return resid(load_o(y, c, x), Itile[y * CW + cc]); };
-    auto r_left = [&](int y) { return resid(load_o(y, 0, x0 - 1), Ihalo[y]); };
-    auto r_right = [&](int y) { return resid(load_o(y, CW + 1, x0 + CW), Ihalo[NL + y]); };
+    auto r_own = [&](int y) { return resid(load_o(y, c), Itile[y * CW + cc]); };
+    auto r_left = [&](int y) { return resid(load_o(y, 0), Ihalo[y]); };
+    auto r_right = [&](int y) { return resid(load_o(y, CW + 1), Ihalo[NL + y]); };
     auto huber2 = [&](float dx, float dy) -> OmegaOut {
       OmegaOut o;
       if constexpr (ISO != 0) {
@@ -298,61 +299,61 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       float wl_x = 0.f;
       if (has_left) {
         const float rl = r_left(y);
-        const float dxl = resid(load_o(y, 1, x0), Itile[y * CW]) - rl;
+        const float dxl = resid(load_o(y, 1), Itile[y * CW]) - rl;
         const float dyl = (y < NL - 1) ? r_left(y + 1) - rl : 0.f;
         wl_x = huber2(dxl, dyl).wx;
       }
       Hx[NL + y] = wl_x;
     }
     // rows outside the strip, read before the barrier
-    const float r_above = (ybeg >= 1) ? r_own(ybeg - 1) : 0.f;
-    const float r_below = (yend < NL) ? r_own(yend) : 0.f;
+    const float r_above = (strip && ybeg >= 1) ? r_own(ybeg - 1) : 0.f;
+    const float r_below = (strip && yend < NL) ? r_own(yend) : 0.f;
     __syncthreads();
-    float2 o_cur = load_o(ybeg, c, x);
-    float r_cur = resid(o_cur, Itile[ybeg * CW + cc]);
-    // omega_y at the row above the strip
-    float wy_prev = 0.f;
-    if (ybeg >= 1) {
-      float rr = __shfl_down_sync(0xffffffffu, r_above, 1);
-      if (wl == CW - 1) rr = Hx[ybeg - 1];
-      const float dx = (x < NL - 1) ? rr - r_above : 0.f;
-      wy_prev = huber2(dx, r_cur - r_above).wy;
-    }
-    // one row of look-ahead held in registers, loaded an iteration before it is used
-    float2 o_nxt = (ybeg + 1 < yend) ? load_o(ybeg + 1, c, x) : make_float2(0.f, 0.f);
-    float i_nxt = (ybeg + 1 < yend) ? Itile[(ybeg + 1) * CW + cc] : 0.f;
-#pragma unroll 2
-    for (int y = ybeg; y < yend; ++y) {
-      // loads for row y + 2 (consumed next iteration)
-      float2 o_nn = make_float2(0.f, 0.f);
-      float i_nn = 0.f;
-      if (y + 2 < yend) {
-        o_nn = load_o(y + 2, c, x);
-        i_nn = Itile[(y + 2) * CW + cc];
+    if (strip) {
+      float2 o_cur = load_o(ybeg, c);
+      float r_cur = resid(o_cur, Itile[ybeg * CW + cc]);
+      // omega_y at the row above the strip (0 above the first row)
+      float wy_prev = 0.f;
+      if (ybeg >= 1) {
+        float rr = __shfl_down_sync(0xffffffffu, r_above, 1);
+        if (wl == CW - 1) rr = Hx[ybeg - 1];
+        const float dx = (x < NL - 1) ? rr - r_above : 0.f;
+        wy_prev = huber2(dx, r_cur - r_above).wy;
       }
-      const float r_nxt = (y + 1 < yend) ? resid(o_nxt, i_nxt) : ((y + 1 < NL) ? r_below : 0.f);
-      float rr = __shfl_down_sync(0xffffffffu, r_cur, 1);
-      if (wl == CW - 1) rr = Hx[y];
-      const float dx = (x < NL - 1) ? rr - r_cur : 0.f;
-      const float dy = (y < NL - 1) ? r_nxt - r_cur : 0.f;
-      const OmegaOut w0 = huber2(dx, dy);
-      float wx_left = __shfl_up_sync(0xffffffffu, w0.wx, 1);
-      if (wl == 0) wx_left = Hx[NL + y];
-      if (on) {
-        float w = -w0.wx - w0.wy;
-        if (x >= 1) w += wx_left;
-        if (y >= 1) w += wy_prev;
-        acc += w0.phi;
-        float f = w;
-        if constexpr (FID != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
-        // W times (-1)^(x+y) for the forward fftshift; o_cur already carries the inverse one
-        OC[FftTeam<NL>::pidx(y) * PO + c] = cscale(o_cur, ((x + y) & 1) ? -f : f);
+      // the strip's rows, fully unrolled: only the last row's neighbour below depends on where
+      // the strip lies (the next strip's first row, or the image edge, where dy = 0)
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        const int y = ybeg + i;
+        float2 o_nxt;
+        float r_nxt;
+        if (i + 1 < RPW) {
+          o_nxt = load_o(y + 1, c);
+          r_nxt = resid(o_nxt, Itile[(y + 1) * CW + cc]);
+        } else {
+          o_nxt = o_cur;
+          r_nxt = (yend < NL) ? r_below : r_cur;
+        }
+        float rr = __shfl_down_sync(0xffffffffu, r_cur, 1);
+        if (wl == CW - 1) rr = Hx[y];
+        const float dx = (x < NL - 1) ? rr - r_cur : 0.f;
+        const float dy = r_nxt - r_cur;
+        const OmegaOut w0 = huber2(dx, dy);
+        float wx_left = __shfl_up_sync(0xffffffffu, w0.wx, 1);
+        if (wl == 0) wx_left = Hx[NL + y];  // 0 left of the image
+        if (on) {
+          float w = -w0.wx - w0.wy;
+          w += wx_left;
+          w += wy_prev;
+          acc += w0.phi;
+          float f = w;
+          if constexpr (FID != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
+          OC[FftTeam<NL>::pidx(y) * PO + c] = cscale(o_cur, f);
+        }
+        wy_prev = w0.wy;
+        o_cur = o_nxt;
+        r_cur = r_nxt;
       }
-      wy_prev = w0.wy;
-      o_cur = o_nxt;
-      r_cur = r_nxt;
-      o_nxt = o_nn;
-      i_nxt = i_nn;
     }
   }
   // the warp's cost pair, summed in a fixed order with the other warps' by the cost reduction
