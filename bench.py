@@ -36,7 +36,8 @@ METRIC = "LED sub-image updates/s (K×iters/s) at fixed error vs FP64 oracle; p9
 UNIT = "LED sub-image updates/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "tile_kernel_traffic.json")
-TILE_SOURCES = ["paper_2209_14671_gb300/csrc/tile_kernel.cu", "paper_2209_14671_gb300/csrc/fft.cuh"]
+TILE_SOURCES = ["paper_2209_14671_gb300/csrc/tile_kernel.cu", "paper_2209_14671_gb300/csrc/fft.cuh",
+                "paper_2209_14671_gb300/csrc/reduce.cuh"]
 L2_FLUSH_BYTES = 256 << 20
 
 
