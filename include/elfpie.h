@@ -44,7 +44,8 @@ enum {
   ELF_ENOMEM = -2,    /* device allocation failed */
   ELF_ECUDA = -3,     /* a CUDA runtime call failed; see elf_last_error() */
   ELF_ENUMERIC = -4,  /* a non-finite cost was produced */
-  ELF_ETIMEOUT = -5,  /* a bounded device wait ran out (tensor-core path); the results are invalid */
+  ELF_ETIMEOUT = -5,  /* a bounded device wait ran out (a DSMEM exchange of the tile kernel or the
+                         tensor-core path); the results are invalid */
   ELF_ESTATE = -6     /* call out of order (e.g. elf_step before elf_set_measurements) */
 };
 

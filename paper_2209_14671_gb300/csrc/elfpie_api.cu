@@ -86,7 +86,7 @@ struct elf_handle_s {
   // tensor-core tile path (tile_dft = 1)
   float2 *tc_X = nullptr, *tc_Y = nullptr, *tc_O = nullptr, *tc_W = nullptr, *tc_Z = nullptr, *tc_G = nullptr;
   float2 *tc_Einv = nullptr, *tc_Ffwd = nullptr;
-  int* tc_err = nullptr;
+  int* tc_err = nullptr;  // device error flag of the bounded waits (tile exchanges, tensor-core path)
   float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
   double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
   std::vector<void*> allocs;
@@ -179,6 +179,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ta.tw = h->tw_n;
   ta.G = h->G;
   ta.cost_ff = h->cost_ff;
+  ta.err = h->tc_err;
   ta.I_out = nullptr;
   ta.N = h->N;
   ta.K = h->K;
@@ -555,6 +556,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->pupil_unit, B))) return rc;
   if ((rc = dalloc(h, &h->cost_fid, (size_t)K))) return rc;
   if ((rc = dalloc(h, &h->cost_ff, (size_t)K * h->cs * tile_warps(n)))) return rc;
+  if ((rc = dalloc(h, &h->tc_err, 1))) return rc;
+  ELF_CK(cudaMemset(h->tc_err, 0, sizeof(int)));
   if ((rc = dalloc(h, &h->cost_h, (size_t)2 * h->hblocks))) return rc;
   if ((rc = dalloc(h, &h->ring, (size_t)3 * kCostRing))) return rc;
   if ((rc = dalloc(h, &h->weights, 2))) return rc;
@@ -572,7 +575,6 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
     if ((rc = dalloc(h, &h->tc_W, Kz * kTcN * kTcN))) return rc;
     if ((rc = dalloc(h, &h->tc_Z, Kz * kTcBand * kTcN))) return rc;
     if ((rc = dalloc(h, &h->tc_G, Kz * kTcBand * kTcBand))) return rc;
-    if ((rc = dalloc(h, &h->tc_err, 1))) return rc;
     // band DFT matrices in FP64: rows j < nb hold frequency Blo + j, the rest are zero
     std::vector<float2> Ei((size_t)kTcBand * kTcN, make_float2(0.f, 0.f)), Ff(Ei);
     const double pi = 3.14159265358979323846;
@@ -584,7 +586,6 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
       }
     if ((rc = upload(h, &h->tc_Einv, Ei))) return rc;
     if ((rc = upload(h, &h->tc_Ffwd, Ff))) return rc;
-    ELF_CK(cudaMemset(h->tc_err, 0, sizeof(int)));
     ELF_CK(prepare_tc());
   }
   ELF_CK(prepare_tile(n, h->rowsA));
@@ -731,7 +732,7 @@ int elf_get_costs(elf_handle h, double* out, int max_iter) {
   if (h->tc_err) {
     int bad = 0;
     ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (bad) return set_error(ELF_ETIMEOUT, "a tensor-core wait ran out; results are invalid");
+    if (bad) return set_error(ELF_ETIMEOUT, "a bounded device wait ran out; results are invalid");
   }
   int count = t < max_iter ? t : max_iter;
   if (count > kCostRing) count = kCostRing;
@@ -821,7 +822,7 @@ int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* co
   if (h->tc_err) {
     int bad = 0;
     ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (bad) return set_error(ELF_ETIMEOUT, "a tensor-core wait ran out; results are invalid");
+    if (bad) return set_error(ELF_ETIMEOUT, "a bounded device wait ran out; results are invalid");
   }
   if (costs3) std::memcpy(costs3, c, sizeof(c));
   for (double v : c)
@@ -854,6 +855,7 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   ta.tw = h->tw_n;
   ta.I_out = dst;
   ta.cost_ff = h->cost_ff;
+  ta.err = h->tc_err;
   ta.N = h->N;
   ta.K = h->K;
   ta.S = h->S;
@@ -867,6 +869,9 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (staging) cudaFree(staging);
   if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("elf_simulate: ") + cudaGetErrorString(e));
+  int bad = 0;
+  ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bad) return set_error(ELF_ETIMEOUT, "a bounded device wait ran out; results are invalid");
   return ELF_OK;
 }
 

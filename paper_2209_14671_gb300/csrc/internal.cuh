@@ -21,6 +21,7 @@ struct TileArgs {
   const float2* tw;       // n team twiddles tw[k1 * Q + l] = e^{-2 pi i l k1 / n}
   float2* G;              // K x S tile gradients on the support (gradient mode)
   float2* cost_ff;        // K x CS x warps fidelity cost partials, (hi, lo) float pairs
+  int* err;               // set to 1 when a bounded wait of a DSMEM exchange ran out
   float* I_out;           // K x n x n predicted intensities (simulate mode)
   int N, K, S, Blo, nb, rowsA;
   float scale;            // 1 / (u^2 n^2)

@@ -55,14 +55,6 @@ __host__ __device__ constexpr int oc_pitch(int n) {
 // largest power of two <= w (the warps that walk row strips in the stencil pass)
 __host__ __device__ constexpr int pow2_floor(int w) { return w >= 16 ? 16 : w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1; }
 
-template <int CS>
-__device__ __forceinline__ void cluster_barrier() {
-  if constexpr (CS > 1) {
-    cg::this_cluster().sync();
-  } else {
-    __syncthreads();
-  }
-}
 
 // The two halves of a cluster barrier (no memory ordering: used only to know that every CTA
 // of the cluster is running); every thread of every CTA executes both.
@@ -75,14 +67,47 @@ __device__ __forceinline__ void cluster_wait() {
   if constexpr (CS > 1) asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
 }
 
-template <int CS, typename T>
-__device__ __forceinline__ T* remote(T* p, int rank) {
-  if constexpr (CS > 1) {
-    return cg::this_cluster().map_shared_rank(p, rank);
-  } else {
-    return p;
-  }
+// ---- asynchronous DSMEM exchange: st.async stores into another CTA's shared memory, each
+// counted in bytes on an mbarrier of the receiving CTA, which waits for the byte count it
+// expects.  The sender never waits for its stores (no release fence); every wait is bounded.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
 }
+
+__device__ __forceinline__ void st_async_f2(uint32_t raddr, float2 v, uint32_t rmbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "f"(v.x), "f"(v.y), "r"(rmbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_expect(uint64_t* bar, uint32_t bytes) {
+  const uint32_t a = smem_u32(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+constexpr long kTileSpinLimit = 1L << 22;
+
+// Wait (acquire, cluster scope) for phase 0 of bar; on time-out flag the error and go on.
+__device__ __forceinline__ void mbar_wait_or_flag(uint64_t* bar, int* err) {
+  const uint32_t a = smem_u32(bar);
+  for (long it = 0; it < kTileSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a)
+        : "memory");
+    if (ok) return;
+  }
+  atomicExch(err, 1);
+}
+
 
 // The smoothed normaliser of Eq. 12 (reading A7) at one pixel: omega = d / max(|d|, tau),
 // phi = |d| (|d| >= tau) or |d|^2/(2 tau) + tau/2 (per component when anisotropic).
@@ -149,14 +174,26 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  // Every CTA of the cluster must be running before the first remote store: arrive now, wait
-  // just before the stage A pushes, so that the barrier's latency overlaps the crop loads and
-  // the first transforms.
+  const int b0 = crank * a.rowsA;
+  const int nrows = max(0, min(a.nb - b0, a.rowsA));
+  // mbarriers of the two exchanges into this CTA: [0] the stage A rows of its owned and halo
+  // columns (every band row, CW columns plus a halo column on each inner side), [1] its stage C
+  // rows (all n columns of each of its band rows)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Hx + 2 * NL);
+  if constexpr (CS > 1) {
+    if (tid == 0) {
+      const int cols = CW + (crank > 0 ? 1 : 0) + (crank < CS - 1 ? 1 : 0);
+      mbar_init_expect(&mbar[0], (uint32_t)(a.nb * cols * 8));
+      mbar_init_expect(&mbar[1], (uint32_t)(nrows * NL * 8));
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+  }
+  // Every CTA of the cluster must be running, with its mbarriers initialised, before the first
+  // remote store: arrive now, wait just before the stage A pushes, so that the barrier's latency
+  // overlaps the crop loads and the first transforms.
   cluster_arrive<CS>();
 
   const int2 org = a.origin[led];
-  const int b0 = crank * a.rowsA;
-  const int nrows = max(0, min(a.nb - b0, a.rowsA));
 
   // ---- A: inverse row transforms of this CTA's band rows, pushed into the column owners
   for (int base = 0; base < a.rowsA; base += NTEAM) {
@@ -205,10 +242,15 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
           const int x = lane + Q * m + PL * k2;
           const float2 val = v[m * Q + k2];
           const int own = x / CW, c = x - own * CW + 1;
-          remote<CS>(OC, own)[py * PO + c] = val;
-          if (CS > 1) {
-            if (c == CW && own + 1 < CS) remote<CS>(OC, own + 1)[py * PO] = val;        // left halo of the next CTA
-            if (c == 1 && own > 0) remote<CS>(OC, own - 1)[py * PO + CW + 1] = val;     // right halo of the previous
+          if constexpr (CS > 1) {
+            const uint32_t e = smem_u32(OC + py * PO + c), m = smem_u32(&mbar[0]);
+            st_async_f2(mapa_u32(e, own), val, mapa_u32(m, own));
+            if (c == CW && own + 1 < CS)  // left halo of the next CTA
+              st_async_f2(mapa_u32(e - 8u * CW, own + 1), val, mapa_u32(m, own + 1));
+            if (c == 1 && own > 0)        // right halo of the previous CTA
+              st_async_f2(mapa_u32(e + 8u * CW, own - 1), val, mapa_u32(m, own - 1));
+          } else {
+            OC[py * PO + c] = val;
           }
         }
       }
@@ -219,7 +261,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     __syncthreads();
     cluster_wait<CS>();
   }
-  cluster_barrier<CS>();
+  if constexpr (CS > 1) {
+    mbar_wait_or_flag(&mbar[0], a.err);  // every band row of this CTA's columns has landed
+  } else {
+    __syncthreads();
+  }
 
   // ---- B: inverse column transforms of the owned + halo columns (all local now);
   // only the support band rows hold data, the rest are zeros the transform never reads
@@ -372,11 +418,21 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   __syncthreads();
   for (int b = warp; b < a.nb; b += NW) {
     const int own = b / a.rowsA, lb = b - own * a.rowsA;
-    float2* dst = remote<CS>(A1, own) + lb * RP;
     const int py = FftTeam<NL>::pidx(a.Blo + b);
-    for (int cc = wl; cc < CW; cc += 32) dst[FftTeam<NL>::pidx(x0 + cc)] = OC[py * PO + cc + 1];
+    for (int cc = wl; cc < CW; cc += 32) {
+      float2* dst = A1 + lb * RP + FftTeam<NL>::pidx(x0 + cc);
+      if constexpr (CS > 1) {
+        st_async_f2(mapa_u32(smem_u32(dst), own), OC[py * PO + cc + 1], mapa_u32(smem_u32(&mbar[1]), own));
+      } else {
+        *dst = OC[py * PO + cc + 1];
+      }
+    }
   }
-  cluster_barrier<CS>();
+  if constexpr (CS > 1) {
+    mbar_wait_or_flag(&mbar[1], a.err);  // all n columns of this CTA's band rows have landed
+  } else {
+    __syncthreads();
+  }
 
   // ---- C: forward row transforms of this CTA's band rows; the support pixels go
   // from the transform's registers straight to G
@@ -429,7 +485,7 @@ size_t tile_smem_bytes(int n, int cs, int rowsA) {
   const size_t rp = fft_padded_length(n);
   const size_t cw = n / cs;
   return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
-         4 * 2 * (size_t)n;
+         4 * 2 * (size_t)n + 16;  // ... + Hx + two mbarriers
 }
 
 int tile_warps(int n) { return tile_threads(n) / 32; }
