@@ -84,8 +84,9 @@ struct elf_handle_s {
   int *t_dev = nullptr, *flag = nullptr;
   size_t device_bytes = 0;  // sum of this handle's device allocations
   // tensor-core tile path (tile_dft = 1)
-  float2 *tc_X = nullptr, *tc_Y = nullptr, *tc_O = nullptr, *tc_W = nullptr, *tc_Z = nullptr, *tc_G = nullptr;
-  float2 *tc_Einv = nullptr, *tc_Ffwd = nullptr;
+  unsigned char *tc_iX = nullptr, *tc_iY = nullptr, *tc_iW = nullptr, *tc_iZ = nullptr;  // operand images
+  unsigned char* tc_c[4] = {nullptr, nullptr, nullptr, nullptr};                       // constant images
+  float2* tc_Ot = nullptr;
   int* tc_err = nullptr;  // device error flag of the bounded waits (tile exchanges, tensor-core path)
   float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
   double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
@@ -203,14 +204,15 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     tc.row_cnt = h->row_cnt;
     tc.row_off = h->row_off;
     tc.meas = h->I;
-    tc.Einv = h->tc_Einv;
-    tc.Ffwd = h->tc_Ffwd;
-    tc.X = h->tc_X;
-    tc.Y = h->tc_Y;
-    tc.O = h->tc_O;
-    tc.Wt = h->tc_W;
-    tc.Z = h->tc_Z;
-    tc.Gt = h->tc_G;
+    tc.cA1 = h->tc_c[0];
+    tc.cB2 = h->tc_c[1];
+    tc.cA3 = h->tc_c[2];
+    tc.cB4 = h->tc_c[3];
+    tc.iX = h->tc_iX;
+    tc.iY = h->tc_iY;
+    tc.iW = h->tc_iW;
+    tc.iZ = h->tc_iZ;
+    tc.Ot = h->tc_Ot;
     tc.G = h->G;
     tc.costpart = h->cost_fid;
     tc.err = h->tc_err;
@@ -569,23 +571,16 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->gp, 2))) return rc;
   if (h->opt.tile_dft) {
     const size_t Kz = (size_t)K;
-    if ((rc = dalloc(h, &h->tc_X, Kz * kTcBand * kTcBand))) return rc;
-    if ((rc = dalloc(h, &h->tc_Y, Kz * kTcBand * kTcN))) return rc;
-    if ((rc = dalloc(h, &h->tc_O, Kz * kTcN * kTcN))) return rc;
-    if ((rc = dalloc(h, &h->tc_W, Kz * kTcN * kTcN))) return rc;
-    if ((rc = dalloc(h, &h->tc_Z, Kz * kTcBand * kTcN))) return rc;
-    if ((rc = dalloc(h, &h->tc_G, Kz * kTcBand * kTcBand))) return rc;
-    // band DFT matrices in FP64: rows j < nb hold frequency Blo + j, the rest are zero
-    std::vector<float2> Ei((size_t)kTcBand * kTcN, make_float2(0.f, 0.f)), Ff(Ei);
-    const double pi = 3.14159265358979323846;
-    for (int j = 0; j < h->nb; ++j)
-      for (int x = 0; x < kTcN; ++x) {
-        const double ang = 2.0 * pi * (double)(((long)(h->Blo + j) * x) % kTcN) / (double)kTcN;
-        Ei[(size_t)j * kTcN + x] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        Ff[(size_t)j * kTcN + x] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
-      }
-    if ((rc = upload(h, &h->tc_Einv, Ei))) return rc;
-    if ((rc = upload(h, &h->tc_Ffwd, Ff))) return rc;
+    if ((rc = dalloc(h, &h->tc_iX, Kz * kTcImgX))) return rc;
+    if ((rc = dalloc(h, &h->tc_iY, Kz * kTcImgY))) return rc;
+    if ((rc = dalloc(h, &h->tc_iW, Kz * kTcImgW))) return rc;
+    if ((rc = dalloc(h, &h->tc_iZ, Kz * kTcImgZ))) return rc;
+    if ((rc = dalloc(h, &h->tc_Ot, Kz * kTcN * kTcN))) return rc;
+    // rows 64..127 of the Z images are never written by the kernels and must read as zero
+    ELF_CK(cudaMemset(h->tc_iZ, 0, Kz * kTcImgZ));
+    // band DFT operands, FP64 on the host, split into BF16 hi + lo images
+    for (int i = 0; i < 4; ++i)
+      if ((rc = upload(h, &h->tc_c[i], tc_constant_image(i, h->Blo, h->nb)))) return rc;
     ELF_CK(prepare_tc());
   }
   ELF_CK(prepare_tile(n, h->rowsA));

@@ -1,6 +1,8 @@
 // Internal interfaces between the host API (elfpie_api.cu) and the kernels.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 namespace elf {
@@ -38,13 +40,18 @@ cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
 // ---------------------------------------------------------------- tensor-core tile path (tc_dft.cu)
 constexpr int kTcN = 128;     // tile side of the tensor-core path
 constexpr int kTcBand = 64;   // padded band of support rows / columns
+// BF16 hi/lo operand images (tc_dft.cu): R rows x KR real K take R * KR * 4 bytes
+constexpr size_t kTcImgX = (size_t)kTcBand * 2 * kTcBand * 4;  // X: 64 rows, K = 128
+constexpr size_t kTcImgY = (size_t)kTcN * 2 * kTcBand * 4;     // Y' (and one gemm-1 A): 128 rows, K = 128
+constexpr size_t kTcImgW = (size_t)kTcN * 2 * kTcN * 4;        // W' (and one gemm-3 A): 128 rows, K = 256
+constexpr size_t kTcImgZ = (size_t)kTcN * 2 * kTcN * 4;        // Z: 128 rows (64 used), K = 256
 struct TcArgs {
   const float2* psi; const float2* pupil; const int2* origin;
   const int* row_xs; const int* row_cnt; const int* row_off;
   const float* meas;
-  const float2* Einv;   // 64 x 128: e^{+2 pi i (Blo + j) x / n}, zero rows j >= nb
-  const float2* Ffwd;   // 64 x 128: e^{-2 pi i (Blo + j) x / n}, zero rows j >= nb
-  float2 *X, *Y, *O, *Wt, *Z, *Gt;  // per-LED intermediates
+  const unsigned char *cA1, *cB2, *cA3, *cB4;  // constant operand images (tc_constant_image 0..3)
+  unsigned char *iX, *iY, *iW, *iZ;           // per-LED data operand images
+  float2* Ot;           // per-LED O' = transposed raw IDFT (128 x 128)
   float2* G;            // K x S output on the support
   double* costpart;     // K fidelity cost partials
   int* err;             // set when a bounded wait runs out
@@ -52,6 +59,9 @@ struct TcArgs {
   float scale, tau, eta;
   int fidelity, iso;
 };
+// Constant operand images, built on the host in FP64 and split into BF16 hi + lo:
+// 0 = gemm 1's two A, 1 = gemm 2's B, 2 = gemm 3's two A, 3 = gemm 4's B.
+std::vector<unsigned char> tc_constant_image(int which, int Blo, int nb);
 cudaError_t prepare_tc();
 cudaError_t launch_tc_tile(const TcArgs& a, cudaStream_t s);
 

@@ -73,14 +73,18 @@ std::string make_key(const elf_problem& p, const elf_options& o) {
 }
 
 // Device bytes a handle of this problem will hold (the allocations of elf_create).
-size_t estimate_bytes(const elf_problem& p) {
+size_t estimate_bytes(const elf_problem& p, int tile_dft) {
   const size_t n = p.n_lowres, N = (size_t)p.n_lowres * p.upsample, K = p.n_led;
   const size_t A = N * N, B = n * n, S = B;  // the support is at most the whole pupil grid
   // Psi-sized: 6 complex + 2 real; per LED: I and G plus the Eq. 18 partials and the tile kernel's
   // per-warp cost pairs; pupil-sized: 8 complex + 3 real/int; 1 MB for the remaining tables,
   // twiddles and reductions
   const size_t cost_pairs = 8 * (size_t)elf::tile_cluster_size((int)n) * (size_t)elf::tile_warps((int)n);
-  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + (1u << 20);
+  // the tensor-core tile path adds its per-LED operand images and O', and 640 KB of constants
+  const size_t tc = tile_dft ? K * (elf::kTcImgX + elf::kTcImgY + elf::kTcImgW + elf::kTcImgZ +
+                                    8 * (size_t)elf::kTcN * elf::kTcN) + (640u << 10)
+                             : 0;
+  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + (1u << 20);
 }
 
 }  // namespace
@@ -141,7 +145,7 @@ int admit_one(elf_server s) {
     p = it->second;
     s->idle.erase(it);
   } else {
-    const size_t est = estimate_bytes(r->prob);
+    const size_t est = estimate_bytes(r->prob, r->opt.tile_dft);
     if (!make_room(s, est)) return 0;
     if (cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail(ELF_ECUDA, "cudaStreamCreate failed");
@@ -195,7 +199,8 @@ int elf_server_submit(elf_server s, const elf_problem* prob, const elf_options* 
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
   for (Request* q : s->active)
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
-  if (estimate_bytes(*prob) > s->budget) return fail(ELF_ENOMEM, "request larger than the memory budget");
+  if (estimate_bytes(*prob, opt ? opt->tile_dft : 0) > s->budget)
+    return fail(ELF_ENOMEM, "request larger than the memory budget");
   Request* r = new Request();
   r->tag = tag;
   r->prob = *prob;
