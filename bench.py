@@ -252,8 +252,10 @@ def precision_leg(torch, dev):
             t_tile.append(st["tile"])
         res[td] = (float(np.median(t_it)), float(np.median(t_tile)))
         elf.close()
-    # tile GEMM work per LED (M padded to 128): 2 M (2 N) (6 K) over the four products
-    flop = w["K"] * 2 * 128 * (256 * 384 + 256 * 384 + 256 * 768 + 128 * 768)
+    # tile GEMM work per LED as executed (M = 128, three BF16 products per real product):
+    # 2 M N K over gemm 1 (two A, N = 64, K = 3 x 128), gemm 2 (N = 256, K = 3 x 128),
+    # gemm 3 (two A, N = 128, K = 3 x 256) and gemm 4 (N = 128, K = 3 x 256)
+    flop = w["K"] * 2 * 128 * (2 * 64 * 384 + 256 * 384 + 2 * 128 * 768 + 128 * 768)
     diff = float(np.linalg.norm(psi[1] - psi[0]) / np.linalg.norm(psi[0]))
     return {"workload": w["name"], "fp32_fft_ms_per_iter": res[0][0], "tensor_core_ms_per_iter": res[1][0],
             "fp32_fft_tile_ms": res[0][1], "tensor_core_tile_ms": res[1][1],

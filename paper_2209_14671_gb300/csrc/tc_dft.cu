@@ -364,13 +364,13 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const TcArgs a) {
 // W' = o' f needs no (-1)^(x+y) factor: the inverse shift's sign and the forward shift's sign
 // multiply to 1.  W' goes to the image of gemm 3's B (128 rows x, K = [Re W' | Im W'] over y);
 // FP64-accurate cost partial per LED.
-__global__ void __launch_bounds__(512) tc_stencil_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(1024) tc_stencil_kernel(const TcArgs a) {
   constexpr int n = kTcN, P = n + 1;  // shared-memory pitch: columns and rows both conflict-free
   extern __shared__ float s_f[];
   float* R = s_f;          // residual, R[y * P + x]
   float* WX = R + n * P;   // omega_x
   float* WY = WX + n * P;  // omega_y
-  __shared__ float red[2 * 16];
+  __shared__ float red[2 * 32];
   const int b = blockIdx.x, tid = threadIdx.x;
   const float2* Ot = a.Ot + (size_t)b * n * n;
   const float* I = a.meas + (size_t)b * n * n;
@@ -563,7 +563,7 @@ cudaError_t launch_tc_tile(const TcArgs& a, cudaStream_t s) {
   g.B = a.cB2; g.sB = 0;
   g.out = nullptr; g.sOut = 0;
   if ((e = gemm<1, 2 * kTcN, 2 * kTcBand, kOT>(g, K, s)) != cudaSuccess) return e;
-  tc_stencil_kernel<<<K, 512, kStencilSmem, s>>>(a);
+  tc_stencil_kernel<<<K, 1024, kStencilSmem, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // gemm 3: Z[k_y][x] = sum_y F[k_y][y] W'[x][y]              (A: F, two images; B: W')
   g.A = a.cA3; g.sA = 0; g.A2off = (long)kTcImgW;
