@@ -54,7 +54,7 @@ struct elf_handle_s {
   double dk = 0.0;
   elf_options opt{};
   cudaStream_t user = nullptr, cap = nullptr, aux = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr;
   bool have_meas = false;
   bool tracing = false;
   int graph_kernels = 0;
@@ -233,6 +233,20 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   }
   ELF_MARK(s0, ELF_STAGE_TILE, 1);
 
+  // Eq. 8 costs on the auxiliary stream once the Hessian partials (same stream) and the tile
+  // kernel's partials exist, beside the gather and pupil kernels below
+  ELF_CK(cudaEventRecord(h->ev_tile, s0));
+  ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_tile, 0));
+  ELF_MARK(h->aux, ELF_STAGE_COST, 0);
+  {
+    const bool tc = h->opt.tile_dft != 0;
+    ELF_CK(launch_cost_reduce(h->cost_fid, tc ? h->K : 0, h->cost_ff, tc ? 0 : h->K * h->cs * tile_warps(h->n),
+                              h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev,
+                              mode == 1 ? h->out3 : nullptr, h->aux));
+  }
+  ELF_MARK(h->aux, ELF_STAGE_COST, 1);
+  ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
+
   PupilArgs pa{};
   pa.G = h->G;
   pa.psi = psi;
@@ -304,13 +318,9 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
                              cudaMemcpyDeviceToDevice, s0));
     ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 1);
   }
-  ELF_MARK(s0, ELF_STAGE_COST, 0);
-  const bool tc = h->opt.tile_dft != 0;
-  ELF_CK(launch_cost_reduce(h->cost_fid, tc ? h->K : 0, h->cost_ff, tc ? 0 : h->K * h->cs * tile_warps(h->n),
-                            h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr,
-                            h->t_dev, mode == 1 ? h->out3 : nullptr, mode == 0 ? 1 : 0, h->bc, h->gp,
-                            h->opt.gamma1, h->opt.gamma2, s0));
-  ELF_MARK(s0, ELF_STAGE_COST, 1);
+  // the cost reduction has read t before the iteration is closed
+  ELF_CK(cudaStreamWaitEvent(s0, h->ev_cost, 0));
+  if (mode == 0) ELF_CK(launch_advance(h->t_dev, h->bc, h->gp, h->opt.gamma1, h->opt.gamma2, s0));
   ELF_MARK(s0, ELF_STAGE_ITERATION, 1);
   return ELF_OK;
 }
@@ -403,6 +413,8 @@ void elf_destroy(elf_handle h) {
     if (ev) cudaEventDestroy(ev);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_tile) cudaEventDestroy(h->ev_tile);
+  if (h->ev_cost) cudaEventDestroy(h->ev_cost);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->aux) cudaStreamDestroy(h->aux);
   delete h;
@@ -520,6 +532,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   ELF_CK(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_high));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_tile, cudaEventDisableTiming));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_cost, cudaEventDisableTiming));
   for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));
 
   // device memory

@@ -133,9 +133,8 @@ cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
-                               double* ring,
-                               int* t_dev, double* out3, int advance, float* bc, double* gp, double g1,
-                               double g2, cudaStream_t s);
+                               double* ring, const int* t_dev, double* out3, cudaStream_t s);
+cudaError_t launch_advance(int* t_dev, float* bc, double* gp, double g1, double g2, cudaStream_t s);
 cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
