@@ -53,8 +53,9 @@ struct elf_handle_s {
   int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;
   double dk = 0.0;
   elf_options opt{};
-  cudaStream_t user = nullptr, cap = nullptr, aux = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr;
+  cudaStream_t user = nullptr, cap = nullptr, aux = nullptr, paux = nullptr;  // paux: pupil chain
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr, ev_pp = nullptr,
+              ev_pu = nullptr;
   bool have_meas = false;
   bool tracing = false;
   int graph_kernels = 0;
@@ -274,10 +275,20 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.g2 = (float)h->opt.gamma2;
   pa.eta = (float)h->opt.eta_opt;
   pa.mode = mode;
+  // the pupil chain (Eq. 18 partials, then the Eq. 19 update of P into pupil_next) on its own
+  // stream; the gather must wait for the partials, which read Psi before the gather updates it,
+  // but not for the pupil update, which overlaps the gather
   if (pupil_path) {
-    ELF_MARK(s0, ELF_STAGE_PUPIL_GRAD, 0);
-    ELF_CK(launch_pupil_partial(pa, s0));
-    ELF_MARK(s0, ELF_STAGE_PUPIL_GRAD, 1);
+    ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_tile, 0));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 0);
+    ELF_CK(launch_pupil_partial(pa, h->paux));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 1);
+    ELF_CK(cudaEventRecord(h->ev_pp, h->paux));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 0);
+    ELF_CK(launch_pupil_update(pa, h->paux));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 1);
+    ELF_CK(cudaEventRecord(h->ev_pu, h->paux));
+    ELF_CK(cudaStreamWaitEvent(s0, h->ev_pp, 0));
   }
 
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_join, 0));
@@ -311,12 +322,11 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_CK(launch_gather(ga, s0));
   ELF_MARK(s0, ELF_STAGE_GATHER, 1);
   if (pupil_path) {
-    ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 0);
-    ELF_CK(launch_pupil_update(pa, s0));
+    // P^t is read by the gather: P^(t+1) replaces it only after both
+    ELF_CK(cudaStreamWaitEvent(s0, h->ev_pu, 0));
     if (mode == 0)
       ELF_CK(cudaMemcpyAsync(h->pupil, h->pupil_next, (size_t)h->n * h->n * sizeof(float2),
                              cudaMemcpyDeviceToDevice, s0));
-    ELF_MARK(s0, ELF_STAGE_PUPIL_UPDATE, 1);
   }
   // the cost reduction has read t before the iteration is closed
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_cost, 0));
@@ -415,6 +425,9 @@ void elf_destroy(elf_handle h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_tile) cudaEventDestroy(h->ev_tile);
   if (h->ev_cost) cudaEventDestroy(h->ev_cost);
+  if (h->ev_pp) cudaEventDestroy(h->ev_pp);
+  if (h->ev_pu) cudaEventDestroy(h->ev_pu);
+  if (h->paux) cudaStreamDestroy(h->paux);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->aux) cudaStreamDestroy(h->aux);
   delete h;
@@ -534,6 +547,9 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   ELF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_tile, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_cost, cudaEventDisableTiming));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_pp, cudaEventDisableTiming));
+  ELF_CK(cudaEventCreateWithFlags(&h->ev_pu, cudaEventDisableTiming));
+  ELF_CK(cudaStreamCreateWithFlags(&h->paux, cudaStreamNonBlocking));
   for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));
 
   // device memory
