@@ -23,6 +23,11 @@ design notes of the repository.  In short:
 * A12 phase = atan2 without unwrapping.  A13 eta_H = 1e-12.  A14 eta_opt = 1e-8.
 * A15 pupil: P~ = G3 (x) P, P_new = mask o (P~ - Delta_P), gradient at P^t.
 * A16 s0_P = 1e-2.
+* A17 gamma / log fidelity (Sec. 6.3): g(x) = x^gamma or ln(x + 1) replaces
+      the identity (Eq. 5) or sqrt (Eq. 4) map of Eq. 3; measured intensities
+      are clamped at 0 before the map, and the slope g'(|o|^2) of the power map
+      takes |o| floored at eta_H, so gamma = 1/2 is exactly the amplitude form.
+      Eqs. 16-17 take g(max(I, 0)) for these maps.
 
 Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
 (brute-force DFT, Parseval, adjoint identities, finite differences, affine null
@@ -43,6 +48,7 @@ __all__ = [
     "grad_op", "grad_adj", "huber", "hessian_op", "hessian_adj",
     "fidelity_cost_grad", "object_from_spectrum", "spectrum_from_object",
     "hessian_cost_grad", "adabelief", "gauss3", "filter3", "alpha_estimate",
+    "scaling_map", "scaling_map_slope",
     "init_state", "iteration", "run", "total_cost", "centre_led",
     "LAPLACE_KERNEL",
 ]
@@ -55,7 +61,10 @@ __all__ = [
 class Options:
     """Hyper-parameters of Sec. 6.2 and the smoothing constants of the readings.
 
-    fidelity: 0 = intensity (Eq. 5, default), 1 = amplitude (Eq. 4).
+    fidelity: 0 = intensity (Eq. 5, default), 1 = amplitude (Eq. 4),
+              2 = power map g(x) = x^g_exponent, 3 = log map g(x) = ln(x + 1)
+              (Sec. 6.3, A17).
+    g_exponent: the gamma of the power map (fidelity 2).
     omega_iso: 1 = isotropic normaliser (Eq. 12 first case), 0 = anisotropic.
     alpha/beta < 0 select the automatic estimate of Eqs. 16-17.
     gamma1, gamma2: the r1, r2 of Sec. 6.2 (0.9 / 0.999).
@@ -75,6 +84,7 @@ class Options:
     eta_h: float = 1e-12
     tau_fid: float = 1e-6
     tau_h: float = 1e-4
+    g_exponent: float = 1.0
 
 
 @dataclasses.dataclass
@@ -237,6 +247,32 @@ def hessian_adj(wxx, wyy, wxy):
 
 
 # ----------------------------------------------------------------------------
+# the pixel-wise scaling g of Eq. 3 beyond Eqs. 4-5 (Sec. 6.3, A17)
+# ----------------------------------------------------------------------------
+def scaling_map(x, opt: Options):
+    """g(x) for a non-negative intensity x: x^gamma (fidelity 2) or ln(x + 1)
+    (fidelity 3), the gamma-correction and logarithmic maps of Sec. 6.3."""
+    x = np.asarray(x, dtype=np.float64)
+    if opt.fidelity == 2:
+        return x ** opt.g_exponent
+    if opt.fidelity == 3:
+        return np.log1p(x)
+    raise ValueError("scaling_map is defined for fidelity 2 and 3")
+
+
+def scaling_map_slope(amp, opt: Options):
+    """g'(|o|^2) as a function of amp = |o|: gamma * max(|o|, eta_H)^(2 gamma - 2)
+    for the power map (the floor of Eq. 10's 1/|o| carried over, A13/A17), and
+    1 / (|o|^2 + 1) for the log map."""
+    amp = np.asarray(amp, dtype=np.float64)
+    if opt.fidelity == 2:
+        return opt.g_exponent * np.maximum(amp, opt.eta_h) ** (2.0 * opt.g_exponent - 2.0)
+    if opt.fidelity == 3:
+        return 1.0 / (amp * amp + 1.0)
+    raise ValueError("scaling_map_slope is defined for fidelity 2 and 3")
+
+
+# ----------------------------------------------------------------------------
 # data fidelity (Eqs. 4-5) and its Wirtinger gradients (Eqs. 9-11, 18)
 # ----------------------------------------------------------------------------
 def fidelity_cost_grad(psi, pupil, I, geo: Geometry, opt: Options, want_tiles=False):
@@ -246,9 +282,12 @@ def fidelity_cost_grad(psi, pupil, I, geo: Geometry, opt: Options, want_tiles=Fa
       o_n = forward_field                                  (Eq. 1)
       r_n = |o_n|^2 - I_n            (intensity, Eq. 5, A8)
           = |o_n| - sqrt(max(I_n,0)) (amplitude, Eq. 4)
+          = g(|o_n|^2) - g(max(I_n,0))  (power / log map, Sec. 6.3, A17)
       d = nabla r_n; (phi, omega) = huber(d)               (Eq. 12, A7)
       W_n = o_n o nabla^T omega            (intensity, Eq. 11)
           = o_n / (2 max(|o_n|, eta_H)) o nabla^T omega     (amplitude, Eq. 10, A11)
+          = g'(|o_n|^2) o_n o nabla^T omega                 (power / log map: chain rule
+            of Eq. 3, d|o|^2/d conj(o) = o)
       G_n = u^-2 n^-2 fftshift(DFT_n(W_n))                 (F_B^H of Eq. 9)
     then (sums in ascending LED order)
       g_Psi = sum_n M_n^T (conj(P) o G_n)                  (Eq. 9)
@@ -267,16 +306,20 @@ def fidelity_cost_grad(psi, pupil, I, geo: Geometry, opt: Options, want_tiles=Fa
         amp = np.abs(o)
         if opt.fidelity == 0:
             r = amp * amp - I[k]
-        else:
+        elif opt.fidelity == 1:
             r = amp - np.sqrt(np.maximum(I[k], 0.0))
+        else:
+            r = scaling_map(amp * amp, opt) - scaling_map(np.maximum(I[k], 0.0), opt)
         dx, dy = grad_op(r)
         phi, (wx, wy) = huber([dx, dy], opt.tau_fid, opt.omega_iso)
         cost += float(np.sum(phi))
         w = grad_adj(wx, wy)
         if opt.fidelity == 0:
             W = o * w
-        else:
+        elif opt.fidelity == 1:
             W = o / (2.0 * np.maximum(amp, opt.eta_h)) * w
+        else:
+            W = scaling_map_slope(amp, opt) * o * w
         G = np.fft.fftshift(np.fft.fft2(W)) / (u * u * n * n)
         if want_tiles:
             tiles[k] = G
@@ -386,11 +429,15 @@ def filter3(p):
 LAPLACE_KERNEL = np.array([[-1.0, 2.0, -1.0], [-2.0, 4.0, -2.0], [-1.0, 2.0, -1.0]])
 
 
-def alpha_estimate(I, amplitude=False):
+def alpha_estimate(I, amplitude=False, opt: Options | None = None):
     """alpha = beta = (1/5) sqrt(pi/2) * mean_n mean_interior |I_n (x) L| (Eq. 16),
-    or of sqrt(I_n) for the amplitude fidelity (Eq. 17).  'valid' 3x3 window."""
+    or of sqrt(I_n) for the amplitude fidelity (Eq. 17), or of g(max(I_n, 0)) for
+    the power and log maps of Sec. 6.3 (A17, when opt.fidelity is 2 or 3).
+    'valid' 3x3 window."""
     I = np.asarray(I, dtype=np.float64)
-    if amplitude:
+    if opt is not None and opt.fidelity in (2, 3):
+        I = scaling_map(np.maximum(I, 0.0), opt)
+    elif amplitude or (opt is not None and opt.fidelity == 1):
         I = np.sqrt(np.maximum(I, 0.0))
     K, h, w = I.shape
     acc = np.zeros((K, h - 2, w - 2))
@@ -446,7 +493,7 @@ def init_state(I, geo: Geometry, k_xy, opt: Options) -> State:
     pupil = geo.support.astype(np.complex128)
     a_auto = None
     if opt.alpha < 0 or opt.beta < 0:
-        a_auto = alpha_estimate(I, amplitude=(opt.fidelity == 1))
+        a_auto = alpha_estimate(I, opt=opt)
     alpha = a_auto if opt.alpha < 0 else float(opt.alpha)
     beta = a_auto if opt.beta < 0 else float(opt.beta)
     return State(

@@ -203,10 +203,11 @@ def _total(psi, pupil, I, geo, opt, alpha, beta):
     return L_fid + alpha * L_A + beta * L_P
 
 
-@pytest.mark.parametrize("fidelity,iso", [(0, 1), (1, 1), (0, 0)])
-def test_gradient_matches_central_differences(fidelity, iso):
+@pytest.mark.parametrize("fidelity,iso,gexp", [(0, 1, 1.0), (1, 1, 1.0), (0, 0, 1.0), (2, 1, 0.375),
+                                               (2, 0, 1.75), (3, 1, 1.0)])
+def test_gradient_matches_central_differences(fidelity, iso, gexp):
     geo, k_xy = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)
-    opt = O.Options(fidelity=fidelity, omega_iso=iso, tau_fid=1e-3, tau_h=1e-3)
+    opt = O.Options(fidelity=fidelity, omega_iso=iso, tau_fid=1e-3, tau_h=1e-3, g_exponent=gexp)
     truth = smooth_object(geo.N, 11)
     I = O.forward_intensity(O.spectrum_from_object(truth), np.ones((16, 16)), geo)
     I = I + 0.01 * np.random.default_rng(12).standard_normal(I.shape)
@@ -244,6 +245,59 @@ def test_zero_gradient_at_the_true_state():
     assert math.isclose(L, geo.K * 16 * 16 * opt.tau_fid / 2, rel_tol=1e-6)
     assert np.abs(g_psi).max() < 1e-9 * np.abs(truth).max()
     assert np.abs(g_p).max() < 1e-9
+
+
+def _fid_problem(seed):
+    geo, _ = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)
+    truth = smooth_object(geo.N, seed)
+    I = O.forward_intensity(O.spectrum_from_object(truth), np.ones((16, 16)), geo)
+    I = I + 0.01 * np.random.default_rng(seed + 1).standard_normal(I.shape)
+    psi = O.spectrum_from_object(smooth_object(geo.N, seed + 2))
+    pupil = geo.support * np.exp(0.2j * np.random.default_rng(seed + 3).standard_normal((16, 16)))
+    return geo, I, psi, pupil
+
+
+def test_power_map_reduces_to_eqs_4_and_5():
+    """Sec. 6.3: the power map g(x) = x^gamma is the intensity fidelity (Eq. 5) at gamma = 1
+    and the amplitude fidelity (Eq. 4) at gamma = 1/2; cost, both gradients and every tile
+    must coincide with those forms, which the finite-difference pins check on their own."""
+    geo, I, psi, pupil = _fid_problem(41)
+    # the maps clamp measurements at 0 (A17) where Eq. 5 does not: compare on I >= 0
+    I = np.maximum(I, 0.0)
+    for gexp, base in ((1.0, 0), (0.5, 1)):
+        a = O.fidelity_cost_grad(psi, pupil, I, geo, O.Options(fidelity=2, g_exponent=gexp), want_tiles=True)
+        b = O.fidelity_cost_grad(psi, pupil, I, geo, O.Options(fidelity=base), want_tiles=True)
+        assert math.isclose(a[0], b[0], rel_tol=1e-12)
+        for x, y in zip(a[1:], b[1:]):
+            assert np.linalg.norm(x - y) <= 1e-12 * np.linalg.norm(y)
+
+
+def test_log_map_is_ln1p_and_its_slope():
+    """g(x) = ln(x + 1) of Sec. 6.3 and g' = 1/(x + 1), checked against math.log and a central
+    difference of math.log at a few points."""
+    opt = O.Options(fidelity=3)
+    for x in (0.0, 1e-9, 0.37, 1.0, 12.5):
+        # near 0, ln(1 + x) = x - x^2/2 + x^3/3 (math.log(1 + x) would lose the low digits)
+        want = x - x * x / 2 + x ** 3 / 3 if x < 1e-3 else math.log(x + 1.0)
+        assert math.isclose(float(O.scaling_map(x, opt)), want, rel_tol=1e-14, abs_tol=1e-300)
+        a = math.sqrt(x)
+        h = 1e-6 * (1.0 + x)
+        fd = (math.log(x + h + 1.0) - math.log(x - h + 1.0)) / (2 * h) if x > h else 1.0 / (x + 1.0)
+        assert math.isclose(float(O.scaling_map_slope(a, opt)), fd, rel_tol=1e-8)
+
+
+@pytest.mark.parametrize("variant", [dict(fidelity=2, g_exponent=0.125), dict(fidelity=3)])
+def test_zero_gradient_at_the_true_state_for_maps(variant):
+    """Noiseless data from the same model: g(|o|^2) - g(I) = 0, so W = 0 for any map."""
+    geo, _ = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)
+    opt = O.Options(**variant)
+    truth = O.spectrum_from_object(smooth_object(geo.N, 23))
+    pupil = geo.support.astype(complex)
+    I = O.forward_intensity(truth, pupil, geo)
+    L, g_psi, g_p, _ = O.fidelity_cost_grad(truth, pupil, I, geo, opt)
+    assert math.isclose(L, geo.K * 16 * 16 * opt.tau_fid / 2, rel_tol=1e-6)
+    assert np.abs(g_psi).max() < 1e-8 * np.abs(truth).max()
+    assert np.abs(g_p).max() < 1e-8
 
 
 # --------------------------------------------------------------------------- Hessian (A6)
@@ -302,6 +356,15 @@ def test_alpha_closed_forms():
     assert math.isclose(want, 2.0053026197048, rel_tol=1e-12)
     # amplitude variant (Eq. 17) takes sqrt first: sqrt(x^4) = x^2
     assert math.isclose(O.alpha_estimate(I ** 2, amplitude=True), want, rel_tol=1e-12)
+    # the maps of Sec. 6.3 (A17) apply g first: (x^8)^(1/4) = x^2 and ln(e^(x^2/100) - 1 + 1)
+    # = x^2 / 100 (kept small so exp stays exact to rounding)
+    assert math.isclose(O.alpha_estimate(I ** 4, opt=O.Options(fidelity=2, g_exponent=0.25)), want,
+                        rel_tol=1e-12)
+    assert math.isclose(O.alpha_estimate(np.expm1(I / 100.0), opt=O.Options(fidelity=3)), want / 100.0,
+                        rel_tol=1e-9)
+    # negative measurements are clamped before the map: g(max(I, 0)) = 0 for I < 0
+    assert O.alpha_estimate(-I, opt=O.Options(fidelity=3)) == 0.0
+    assert O.alpha_estimate(-I, opt=O.Options(fidelity=2, g_exponent=0.5)) == 0.0
 
 
 # --------------------------------------------------------------------------- Eq. 19
