@@ -23,6 +23,9 @@ design notes of the repository.  In short:
 * A12 phase = atan2 without unwrapping.  A13 eta_H = 1e-12.  A14 eta_opt = 1e-8.
 * A15 pupil: P~ = G3 (x) P, P_new = mask o (P~ - Delta_P), gradient at P^t.
 * A16 s0_P = 1e-2.
+* A18 multiplexing (Eq. 1 with M > 1): LEDs in the caller's order, image j is
+      lit by LEDs jM .. jM+M-1 (K a multiple of M); the residual of image j
+      uses sum_m |o_{j,m}|^2; Psi0 comes from the image holding the centre LED.
 * A17 gamma / log fidelity (Sec. 6.3): g(x) = x^gamma or ln(x + 1) replaces
       the identity (Eq. 5) or sqrt (Eq. 4) map of Eq. 3; measured intensities
       are clamped at 0 before the map, and the slope g'(|o|^2) of the power map
@@ -96,10 +99,16 @@ class Geometry:
     offsets: np.ndarray    # int64 [K, 2] = (c_y, c_x) in spectral pixels (A3)
     origins: np.ndarray    # int64 [K, 2] = crop window top-left (row, col) in Psi
     support: np.ndarray    # bool [n, n] pupil support S (A4)
+    mux: int = 1           # M: LEDs lit together per measured image (Eq. 1, A18)
 
     @property
     def K(self) -> int:
         return int(self.offsets.shape[0])
+
+    @property
+    def n_images(self) -> int:
+        """Number of measured images, K / M."""
+        return self.K // self.mux
 
 
 def round_half_away(x):
@@ -108,11 +117,12 @@ def round_half_away(x):
     return (np.sign(x) * np.floor(np.abs(x) + 0.5)).astype(np.int64)
 
 
-def make_geometry(n, u, k_xy, na, wavelength_um, pixel_um) -> Geometry:
+def make_geometry(n, u, k_xy, na, wavelength_um, pixel_um, mux=1) -> Geometry:
     """Crop windows M_n and pupil support of the forward model (Sec. 3.1, Eq. 1).
 
     k_xy: [K, 2] illumination spatial frequency (kx, ky) in cycles/um.
     pixel_um: low-res pixel size at the sample plane.
+    mux: M, the LEDs lit together for one image (A18: image j = LEDs jM .. jM+M-1).
     The spectral spacing is dk = 1/(n*pixel_um) on both grids (N*pixel_um/u = n*pixel_um).
     """
     n = int(n)
@@ -129,11 +139,14 @@ def make_geometry(n, u, k_xy, na, wavelength_um, pixel_um) -> Geometry:
     j = np.arange(n) - n // 2
     rho2 = (j[None, :] ** 2 + j[:, None] ** 2) * dk * dk
     support = rho2 <= (float(na) / float(wavelength_um)) ** 2
-    return Geometry(n=n, u=u, N=N, dk=dk, offsets=offsets, origins=origins, support=support)
+    mux = int(mux)
+    if mux < 1 or k_xy.shape[0] % mux:
+        raise ValueError("the LED count must be a positive multiple of mux")
+    return Geometry(n=n, u=u, N=N, dk=dk, offsets=offsets, origins=origins, support=support, mux=mux)
 
 
 # ----------------------------------------------------------------------------
-# forward model (Sec. 3.1, Eq. 1 with M = 1)
+# forward model (Sec. 3.1, Eq. 1)
 # ----------------------------------------------------------------------------
 def crop(psi, geo: Geometry, led: int):
     """M_n Psi: the n x n window of the centred spectrum for LED ``led``."""
@@ -157,10 +170,11 @@ def forward_field(psi, pupil, geo: Geometry, led: int):
 
 
 def forward_intensity(psi, pupil, geo: Geometry):
-    """Predicted low-res intensities |o_n|^2 for every LED, float64 [K, n, n]."""
-    out = np.empty((geo.K, geo.n, geo.n), dtype=np.float64)
+    """Predicted low-res intensities of Eq. 1, float64 [K/M, n, n]: image j is
+    sum_m |o_{j,m}|^2 over its M LEDs (|o_n|^2 per LED when M = 1)."""
+    out = np.zeros((geo.n_images, geo.n, geo.n), dtype=np.float64)
     for k in range(geo.K):
-        out[k] = np.abs(forward_field(psi, pupil, geo, k)) ** 2
+        out[k // geo.mux] += np.abs(forward_field(psi, pupil, geo, k)) ** 2
     return out
 
 
@@ -278,53 +292,60 @@ def scaling_map_slope(amp, opt: Options):
 def fidelity_cost_grad(psi, pupil, I, geo: Geometry, opt: Options, want_tiles=False):
     """L_fid and its gradients with respect to conj(Psi) and conj(P).
 
-    For each LED (Algorithm 1, inner loops):
-      o_n = forward_field                                  (Eq. 1)
-      r_n = |o_n|^2 - I_n            (intensity, Eq. 5, A8)
-          = |o_n| - sqrt(max(I_n,0)) (amplitude, Eq. 4)
-          = g(|o_n|^2) - g(max(I_n,0))  (power / log map, Sec. 6.3, A17)
-      d = nabla r_n; (phi, omega) = huber(d)               (Eq. 12, A7)
-      W_n = o_n o nabla^T omega            (intensity, Eq. 11)
-          = o_n / (2 max(|o_n|, eta_H)) o nabla^T omega     (amplitude, Eq. 10, A11)
-          = g'(|o_n|^2) o_n o nabla^T omega                 (power / log map: chain rule
-            of Eq. 3, d|o|^2/d conj(o) = o)
-      G_n = u^-2 n^-2 fftshift(DFT_n(W_n))                 (F_B^H of Eq. 9)
+    For each measured image j (Algorithm 1, inner loops), lit by the LEDs
+    m = jM .. jM+M-1 (A18; M = 1 is sequential FPM):
+      o_m = forward_field                                  (Eq. 1)
+      s_j = sum_m |o_m|^2                                  (Eq. 1)
+      r_j = s_j - I_j                (intensity, Eq. 5, A8)
+          = sqrt(s_j) - sqrt(max(I_j,0)) (amplitude, Eq. 4)
+          = g(s_j) - g(max(I_j,0))   (power / log map, Sec. 6.3, A17)
+      d = nabla r_j; (phi, omega) = huber(d)               (Eq. 12, A7)
+      W_m = o_m o nabla^T omega                            (intensity, Eq. 11)
+          = o_m / (2 max(sqrt(s_j), eta_H)) o nabla^T omega (amplitude, Eq. 10, A11)
+          = g'(s_j) o_m o nabla^T omega                    (power / log map: chain rule
+            of Eq. 3, d s_j / d conj(o_m) = o_m)
+      G_m = u^-2 n^-2 fftshift(DFT_n(W_m))                 (F_B^H of Eq. 9)
     then (sums in ascending LED order)
-      g_Psi = sum_n M_n^T (conj(P) o G_n)                  (Eq. 9)
-      g_P   = sum_n conj(M_n Psi) o G_n, masked to S       (Eq. 18)
+      g_Psi = sum_m M_m^T (conj(P) o G_m)                  (Eq. 9)
+      g_P   = sum_m conj(M_m Psi) o G_m, masked to S       (Eq. 18)
+    I holds the K/M measured images.
     Returns (L_fid, g_psi [N,N], g_pupil [n,n], tiles [K,n,n] or None).
     """
-    n, u = geo.n, geo.u
+    n, u, M = geo.n, geo.u, geo.mux
     mask = geo.support
     p_eff = pupil * mask
     g_psi = np.zeros((geo.N, geo.N), dtype=np.complex128)
     g_p = np.zeros((n, n), dtype=np.complex128)
     tiles = np.zeros((geo.K, n, n), dtype=np.complex128) if want_tiles else None
     cost = 0.0
-    for k in range(geo.K):
-        o = forward_field(psi, pupil, geo, k)
-        amp = np.abs(o)
+    for j in range(geo.n_images):
+        leds = range(j * M, (j + 1) * M)
+        fields = [forward_field(psi, pupil, geo, k) for k in leds]
+        s = np.zeros((n, n))
+        for o in fields:
+            s += np.abs(o) ** 2
         if opt.fidelity == 0:
-            r = amp * amp - I[k]
+            r = s - I[j]
         elif opt.fidelity == 1:
-            r = amp - np.sqrt(np.maximum(I[k], 0.0))
+            r = np.sqrt(s) - np.sqrt(np.maximum(I[j], 0.0))
         else:
-            r = scaling_map(amp * amp, opt) - scaling_map(np.maximum(I[k], 0.0), opt)
+            r = scaling_map(s, opt) - scaling_map(np.maximum(I[j], 0.0), opt)
         dx, dy = grad_op(r)
         phi, (wx, wy) = huber([dx, dy], opt.tau_fid, opt.omega_iso)
         cost += float(np.sum(phi))
         w = grad_adj(wx, wy)
-        if opt.fidelity == 0:
-            W = o * w
-        elif opt.fidelity == 1:
-            W = o / (2.0 * np.maximum(amp, opt.eta_h)) * w
-        else:
-            W = scaling_map_slope(amp, opt) * o * w
-        G = np.fft.fftshift(np.fft.fft2(W)) / (u * u * n * n)
-        if want_tiles:
-            tiles[k] = G
-        g_psi += crop_adjoint(np.conj(p_eff) * G, geo, k)
-        g_p += np.conj(crop(psi, geo, k)) * G
+        for k, o in zip(leds, fields):
+            if opt.fidelity == 0:
+                W = o * w
+            elif opt.fidelity == 1:
+                W = o / (2.0 * np.maximum(np.sqrt(s), opt.eta_h)) * w
+            else:
+                W = scaling_map_slope(np.sqrt(s), opt) * o * w
+            G = np.fft.fftshift(np.fft.fft2(W)) / (u * u * n * n)
+            if want_tiles:
+                tiles[k] = G
+            g_psi += crop_adjoint(np.conj(p_eff) * G, geo, k)
+            g_p += np.conj(crop(psi, geo, k)) * G
     g_p = g_p * mask
     return cost, g_psi, g_p, tiles
 
@@ -486,7 +507,7 @@ def init_state(I, geo: Geometry, k_xy, opt: Options) -> State:
     """
     n, u, N = geo.n, geo.u, geo.N
     c = centre_led(k_xy)
-    small = np.fft.fftshift(np.fft.fft2(np.sqrt(np.maximum(I[c], 0.0)))) * (u * u)
+    small = np.fft.fftshift(np.fft.fft2(np.sqrt(np.maximum(I[c // geo.mux], 0.0)))) * (u * u)
     small[0, :] = 0.0
     small[:, 0] = 0.0
     psi = crop_adjoint(small, geo, c)

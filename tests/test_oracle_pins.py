@@ -19,13 +19,16 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json
 
 
 # --------------------------------------------------------------------------- helpers
-def tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0):
-    """Geometry with exact integer LED offsets (k = c * dk) and a pupil of radius na_px."""
+def tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0, mux=1, extra_leds=0):
+    """Geometry with exact integer LED offsets (k = c * dk) and a pupil of radius na_px;
+    `extra_leds` repeats the first LEDs at the end so that K is a multiple of `mux`."""
     dk = 1.0 / n  # pixel 1 um
     c = (np.arange(grid) - (grid - 1) // 2) * step
     cy, cx = np.meshgrid(c, c, indexing="ij")
     k_xy = np.stack([cx.ravel() * dk, cy.ravel() * dk], axis=1)
-    geo = O.make_geometry(n, u, k_xy, na=na_px * dk, wavelength_um=1.0, pixel_um=1.0)
+    if extra_leds:
+        k_xy = np.concatenate([k_xy, k_xy[:extra_leds] + 0.5 * dk], axis=0)
+    geo = O.make_geometry(n, u, k_xy, na=na_px * dk, wavelength_um=1.0, pixel_um=1.0, mux=mux)
     return geo, k_xy
 
 
@@ -298,6 +301,74 @@ def test_zero_gradient_at_the_true_state_for_maps(variant):
     assert math.isclose(L, geo.K * 16 * 16 * opt.tau_fid / 2, rel_tol=1e-6)
     assert np.abs(g_psi).max() < 1e-8 * np.abs(truth).max()
     assert np.abs(g_p).max() < 1e-8
+
+
+# --------------------------------------------------------------------------- multiplexing (Eq. 1, A18)
+def _mux_problem(mux, extra, seed, noise=0.01):
+    geo, k_xy = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0, mux=mux, extra_leds=extra)
+    truth = smooth_object(geo.N, seed)
+    I = O.forward_intensity(O.spectrum_from_object(truth), np.ones((16, 16)), geo)
+    I = I + noise * np.random.default_rng(seed + 1).standard_normal(I.shape)
+    psi = O.spectrum_from_object(smooth_object(geo.N, seed + 2))
+    pupil = geo.support * np.exp(0.2j * np.random.default_rng(seed + 3).standard_normal((16, 16)))
+    return geo, k_xy, I, psi, pupil
+
+
+def test_multiplexed_intensity_is_the_sum_over_its_leds():
+    """Eq. 1: image j of an M-LED multiplexed acquisition is the sum of the M sequential images."""
+    geo2, k_xy, _, psi, pupil = _mux_problem(2, 1, 51)
+    geo1 = O.make_geometry(16, 2, k_xy, na=5.0 / 16, wavelength_um=1.0, pixel_um=1.0)
+    I1 = O.forward_intensity(psi, pupil, geo1)
+    I2 = O.forward_intensity(psi, pupil, geo2)
+    assert I2.shape == (5, 16, 16)
+    assert np.allclose(I2, I1[0::2] + I1[1::2], rtol=1e-13, atol=0)
+    with pytest.raises(ValueError):
+        O.make_geometry(16, 2, k_xy[:9], na=5.0 / 16, wavelength_um=1.0, pixel_um=1.0, mux=2)
+
+
+@pytest.mark.parametrize("mux,extra,variant", [(2, 1, dict()), (3, 0, dict(fidelity=1)),
+                                               (2, 1, dict(fidelity=3, omega_iso=0)),
+                                               (5, 1, dict(fidelity=2, g_exponent=0.6))])
+def test_multiplexed_gradient_matches_central_differences(mux, extra, variant):
+    """Eqs. 9-11 and 18 with M > 1 (the sum over m inside the residual) against central
+    differences of the fidelity along seeded complex directions, for Psi and for P."""
+    geo, _, I, psi, pupil = _mux_problem(mux, extra, 61)
+    opt = O.Options(tau_fid=1e-3, **variant)
+    _, g_psi, g_p, _ = O.fidelity_cost_grad(psi, pupil, I, geo, opt)
+    rng = np.random.default_rng(62)
+    for trial in range(3):
+        d = rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape)
+        d *= np.linalg.norm(psi) / np.linalg.norm(d)
+        h = 1e-7
+        fd = (O.fidelity_cost_grad(psi + h * d, pupil, I, geo, opt)[0]
+              - O.fidelity_cost_grad(psi - h * d, pupil, I, geo, opt)[0]) / (2 * h)
+        an = 2.0 * np.real(np.vdot(g_psi, d))
+        assert abs(fd - an) <= 2e-5 * abs(an) + 1e-9, (trial, fd, an)
+        dp = (rng.standard_normal(pupil.shape) + 1j * rng.standard_normal(pupil.shape)) * geo.support
+        fdp = (O.fidelity_cost_grad(psi, pupil + h * dp, I, geo, opt)[0]
+               - O.fidelity_cost_grad(psi, pupil - h * dp, I, geo, opt)[0]) / (2 * h)
+        anp = 2.0 * np.real(np.vdot(g_p, dp))
+        assert abs(fdp - anp) <= 2e-5 * abs(anp) + 1e-9, (trial, fdp, anp)
+
+
+def test_multiplexed_zero_gradient_at_truth_and_order_within_image():
+    """Noiseless M = 2 data from the same model give W = 0; reordering the LEDs inside each
+    image leaves the cost and g_Psi unchanged and permutes the tiles with the LEDs."""
+    geo, k_xy, _, _, _ = _mux_problem(2, 1, 71)
+    truth = O.spectrum_from_object(smooth_object(geo.N, 72))
+    pupil = geo.support.astype(complex)
+    I = O.forward_intensity(truth, pupil, geo)
+    L, g_psi, g_p, _ = O.fidelity_cost_grad(truth, pupil, I, geo, O.Options())
+    assert math.isclose(L, geo.n_images * 16 * 16 * O.Options().tau_fid / 2, rel_tol=1e-6)
+    assert np.abs(g_psi).max() < 1e-9 * np.abs(truth).max() and np.abs(g_p).max() < 1e-9
+    _, _, I_n, psi, pupil = _mux_problem(2, 1, 73)
+    perm = np.arange(geo.K).reshape(-1, 2)[:, ::-1].ravel()
+    geo_p = O.make_geometry(16, 2, k_xy[perm], na=5.0 / 16, wavelength_um=1.0, pixel_um=1.0, mux=2)
+    a = O.fidelity_cost_grad(psi, pupil, I_n, geo, O.Options(), want_tiles=True)
+    b = O.fidelity_cost_grad(psi, pupil, I_n, geo_p, O.Options(), want_tiles=True)
+    assert math.isclose(a[0], b[0], rel_tol=1e-12)
+    assert np.linalg.norm(a[1] - b[1]) <= 1e-12 * np.linalg.norm(a[1])
+    assert np.linalg.norm(a[3][perm] - b[3]) <= 1e-12 * np.linalg.norm(a[3])
 
 
 # --------------------------------------------------------------------------- Hessian (A6)
