@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision leg")
+    ap.add_argument("--no-fidelity", action="store_true", help="skip the fidelity-variant leg")
     ap.add_argument("--serving-requests", type=int, default=120,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
@@ -265,6 +266,36 @@ def precision_leg(torch, dev):
             "note": "error vs the FP64 oracle: tests/test_gpu_precision.py"}
 
 
+def fidelity_leg(w, I_dev, torch, dev):
+    """The four fidelities on the benchmark workload (same measurements, same initial state):
+    intensity (Eq. 5), amplitude (Eq. 4) and the Sec. 6.3 maps g(x) = x^0.375 and ln(x + 1).
+    Median tile-kernel and iteration times over 10 traced steps after 3 warm-up steps."""
+    from paper_2209_14671_gb300 import elfpie as E
+    stream = torch.cuda.current_stream(dev)
+    variants = [("intensity (Eq. 5)", dict(fidelity=0)), ("amplitude (Eq. 4)", dict(fidelity=1)),
+                ("power x^0.375 (Sec. 6.3)", dict(fidelity=2, g_exponent=0.375)),
+                ("log ln(x+1) (Sec. 6.3)", dict(fidelity=3))]
+    out = {}
+    for name, opts in variants:
+        elf = E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"], options=opts,
+                    stream=stream)
+        elf.set_measurements(I_dev)
+        elf.set_tracing(True)
+        for _ in range(3):
+            elf.step(1)
+        t_it, t_tile = [], []
+        for _ in range(10):
+            elf.step(1)
+            st = elf.stage_times()
+            t_it.append(st["iteration"])
+            t_tile.append(st["tile"])
+        elf.close()
+        out[name] = {"tile_ms": float(np.median(t_tile)), "iteration_ms": float(np.median(t_it)),
+                     "led_updates_per_s": w["K"] / (float(np.median(t_it)) * 1e-3)}
+    return {"workload": w["name"], "variants": out,
+            "note": "traced steps (CUDA events inside the graph); parity: tests/test_gpu_parity.py"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -406,6 +437,10 @@ def run_ours(args):
     if not args.no_precision and world == 1:
         precision = precision_leg(torch, dev)
 
+    fidelity = None
+    if not args.no_fidelity and world == 1:
+        fidelity = fidelity_leg(w, I_dev, torch, dev)
+
     serving = None
     if args.serving_requests > 0:
         serving = serving_leg(args, torch, dev)
@@ -441,6 +476,7 @@ def run_ours(args):
             "e2e": e2e,
             "serving": serving,
             "precision": precision,
+            "fidelity_variants": fidelity,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -68,7 +68,10 @@ typedef struct {
 
 /* Hyper-parameters (Sec. 6.2) and the smoothing constants of the readings. */
 typedef struct {
-  int fidelity;      /* 0 = intensity (Eqs. 5, 11; default), 1 = amplitude (Eqs. 4, 10) */
+  int fidelity;      /* 0 = intensity (Eqs. 5, 11; default), 1 = amplitude (Eqs. 4, 10); Sec. 6.3 scaling maps
+                        of Eq. 3: 2 = power g(x) = x^g_exponent, 3 = log g(x) = ln(x + 1).  For 2 and 3 the
+                        residual is g(|o|^2) - g(max(I, 0)), W = g'(|o|^2) o nabla^T omega with |o| floored
+                        at eta_h in g' of the power map, and Eqs. 16-17 take g(max(I, 0)). */
   int omega_iso;     /* 1 = isotropic normaliser of Eq. 12 (default), 0 = anisotropic */
   int learn_pupil;   /* 1 = update P with Eq. 18 + Eq. 19 (default) */
   int pupil_filter;  /* 1 = 3x3 Gaussian (sigma 1 px) on P before its update (note under Algorithm 1) */
@@ -84,6 +87,7 @@ typedef struct {
   double tau_h;      /* smoothing radius of the Hessian L1 terms (1e-4) */
   int tile_dft;      /* tile transforms: 0 = FP32 FFT (default); 1 = tensor-core DFT, BF16 3-term split with
                         FP32 accumulation (not in the paper; n_lowres = 128 with the support band <= 64 only) */
+  double g_exponent; /* gamma of the power map (fidelity 2), in (0, 8]; 1 by default (Sec. 6.3) */
 } elf_options;
 
 /* Full optimiser state of Eq. 19 for Psi and P (Algorithm 1 keeps nothing else).

@@ -72,6 +72,7 @@ struct elf_handle_s {
   float2 *tw_n = nullptr, *tw_N = nullptr;
   // data and state
   float* I = nullptr;
+  float* Ig = nullptr;  // g(max(I, 0)) for the Sec. 6.3 scaling maps (fidelity 2, 3); else null
   float2 *psi = nullptr, *mu_psi = nullptr;
   float *v_psi = nullptr, *delta_psi = nullptr;
   float2 *pupil = nullptr, *pupil_next = nullptr, *mu_p = nullptr;
@@ -173,7 +174,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   TileArgs ta{};
   ta.psi = psi;
   ta.pupil = pupil;
-  ta.meas = h->I;
+  ta.meas = h->opt.fidelity >= 2 ? h->Ig : h->I;
   ta.origin = h->origin;
   ta.row_xs = h->row_xs;
   ta.row_cnt = h->row_cnt;
@@ -192,6 +193,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
   ta.tau = (float)h->opt.tau_fid;
   ta.eta = (float)h->opt.eta_h;
+  ta.gexp = (float)h->opt.g_exponent;
   ta.fidelity = h->opt.fidelity;
   ta.iso = h->opt.omega_iso;
   ta.mode = 0;
@@ -204,7 +206,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     tc.row_xs = h->row_xs;
     tc.row_cnt = h->row_cnt;
     tc.row_off = h->row_off;
-    tc.meas = h->I;
+    tc.meas = ta.meas;
     tc.cA1 = h->tc_c[0];
     tc.cB2 = h->tc_c[1];
     tc.cA3 = h->tc_c[2];
@@ -226,6 +228,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     tc.scale = ta.scale;
     tc.tau = ta.tau;
     tc.eta = ta.eta;
+    tc.gexp = ta.gexp;
     tc.fidelity = ta.fidelity;
     tc.iso = ta.iso;
     ELF_CK(launch_tc_tile(tc, s0));
@@ -412,6 +415,7 @@ int elf_default_options(elf_options* o) {
   o->tau_fid = 1e-6;
   o->tau_h = 1e-4;
   o->tile_dft = 0;
+  o->g_exponent = 1.0;
   return ELF_OK;
 }
 
@@ -452,7 +456,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   const elf_options& op = h->opt;
   if (!(op.gamma1 >= 0 && op.gamma1 < 1 && op.gamma2 >= 0 && op.gamma2 < 1 && op.tau_fid >= 0 && op.tau_h >= 0 &&
         op.eta_opt >= 0 && op.eta_h >= 0 && op.s0_psi >= 0 && op.s0_pupil >= 0 && std::isfinite(op.alpha) &&
-        std::isfinite(op.beta) && (op.fidelity == 0 || op.fidelity == 1) && (op.tile_dft == 0 || op.tile_dft == 1)))
+        std::isfinite(op.beta) && op.fidelity >= 0 && op.fidelity <= 3 && (op.tile_dft == 0 || op.tile_dft == 1) &&
+        (op.fidelity != 2 || (std::isfinite(op.g_exponent) && op.g_exponent > 0 && op.g_exponent <= 8))))
     return set_error(ELF_EINVAL, "invalid options");
   h->n = n;
   h->u = u;
@@ -567,6 +572,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = upload(h, &h->tw_n, twiddles(n)))) return rc;
   if ((rc = upload(h, &h->tw_N, twiddles(N)))) return rc;
   if ((rc = dalloc(h, &h->I, (size_t)K * B))) return rc;
+  if (op.fidelity >= 2 && (rc = dalloc(h, &h->Ig, (size_t)K * B))) return rc;
   if ((rc = dalloc(h, &h->psi, A))) return rc;
   if ((rc = dalloc(h, &h->mu_psi, A))) return rc;
   if ((rc = dalloc(h, &h->v_psi, A))) return rc;
@@ -646,7 +652,13 @@ int init_state_async(elf_handle h) {
   const size_t B = (size_t)h->n * h->n, A = (size_t)h->N * h->N;
   cudaStream_t s = h->user;
   // alpha = beta (Eqs. 16-17) and the initial state (reading A9)
-  ELF_CK(launch_alpha(h->I, h->K, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
+  if (h->opt.fidelity >= 2) {  // Sec. 6.3 maps: the measured side g(max(I, 0)), also what Eq. 16 reads
+    ELF_CK(launch_gmap(h->I, h->Ig, (size_t)h->K * B, h->opt.fidelity, (float)h->opt.g_exponent, s));
+    ELF_CK(launch_alpha(h->Ig, h->K, h->n, 0, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
+  } else {
+    ELF_CK(launch_alpha(h->I, h->K, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha,
+                        h->opt.beta, s));
+  }
   ELF_CK(launch_init_small(h->I + (size_t)h->centre * B, h->small, h->n, s));
   ELF_CK(launch_fft2(h->small, h->n, false, h->tw_n, s));
   ELF_CK(launch_embed(h->small, h->psi, h->n, h->N, h->origin_h[h->centre].x, h->origin_h[h->centre].y,

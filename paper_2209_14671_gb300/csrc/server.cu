@@ -73,7 +73,7 @@ std::string make_key(const elf_problem& p, const elf_options& o) {
 }
 
 // Device bytes a handle of this problem will hold (the allocations of elf_create).
-size_t estimate_bytes(const elf_problem& p, int tile_dft) {
+size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity) {
   const size_t n = p.n_lowres, N = (size_t)p.n_lowres * p.upsample, K = p.n_led;
   const size_t A = N * N, B = n * n, S = B;  // the support is at most the whole pupil grid
   // Psi-sized: 6 complex + 2 real; per LED: I and G plus the Eq. 18 partials and the tile kernel's
@@ -84,7 +84,10 @@ size_t estimate_bytes(const elf_problem& p, int tile_dft) {
   const size_t tc = tile_dft ? K * (elf::kTcImgX + elf::kTcImgY + elf::kTcImgW + elf::kTcImgZ +
                                     8 * (size_t)elf::kTcN * elf::kTcN) + (640u << 10)
                              : 0;
-  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + (1u << 20);
+  // the Sec. 6.3 scaling maps keep a mapped copy of the measurements
+  const size_t gmap = fidelity >= 2 ? 4 * K * B : 0;
+  return 8 * A * 6 + 4 * A * 2 + 4 * K * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + gmap +
+         (1u << 20);
 }
 
 }  // namespace
@@ -145,7 +148,7 @@ int admit_one(elf_server s) {
     p = it->second;
     s->idle.erase(it);
   } else {
-    const size_t est = estimate_bytes(r->prob, r->opt.tile_dft);
+    const size_t est = estimate_bytes(r->prob, r->opt.tile_dft, r->opt.fidelity);
     if (!make_room(s, est)) return 0;
     if (cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail(ELF_ECUDA, "cudaStreamCreate failed");
@@ -199,7 +202,7 @@ int elf_server_submit(elf_server s, const elf_problem* prob, const elf_options* 
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
   for (Request* q : s->active)
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
-  if (estimate_bytes(*prob, opt ? opt->tile_dft : 0) > s->budget)
+  if (estimate_bytes(*prob, opt ? opt->tile_dft : 0, opt ? opt->fidelity : 0) > s->budget)
     return fail(ELF_ENOMEM, "request larger than the memory budget");
   Request* r = new Request();
   r->tag = tag;

@@ -7,6 +7,8 @@
 //   cost_reduce      Eq. 8's three terms in FP64, fixed order
 //   alpha kernels    Eqs. 16-17 in FP64, fixed order
 //   init kernels     the initial state of elf_set_measurements
+#include <algorithm>
+
 #include "fft.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -505,6 +507,41 @@ cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* pa
   } else {
     alpha_final_kernel<<<1, 256, 0, s>>>(partial, 0, K, n, weights, fixed_alpha, fixed_beta);
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Sec. 6.3 scaling maps
+// The measured side of the residual g(|o|^2) - g(max(I, 0)), mapped once per set of measurements.
+__global__ void gmap_kernel(const float4* __restrict__ I, float4* __restrict__ Ig, size_t n4, int fidelity,
+                            float gexp) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    float4 v = I[i];
+    float* e = reinterpret_cast<float*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float x = fmaxf(e[j], 0.f);
+      e[j] = (fidelity == 2) ? powf(x, gexp) : log1pf(x);
+    }
+    Ig[i] = v;
+  }
+}
+
+__global__ void gmap_tail_kernel(const float* I, float* Ig, size_t b, size_t count, int fidelity, float gexp) {
+  const size_t i = b + threadIdx.x;
+  if (i >= count) return;
+  const float x = fmaxf(I[i], 0.f);
+  Ig[i] = (fidelity == 2) ? powf(x, gexp) : log1pf(x);
+}
+
+cudaError_t launch_gmap(const float* I, float* Ig, size_t count, int fidelity, float gexp, cudaStream_t s) {
+  // I and Ig come from cudaMalloc (256-byte aligned); the last count % 4 elements go one by one
+  const size_t n4 = count / 4;
+  if (n4) {
+    const int blocks = (int)std::min<size_t>((n4 + 255) / 256, 152 * 8);
+    gmap_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(I), reinterpret_cast<float4*>(Ig), n4,
+                                       fidelity, gexp);
+  }
+  if (count % 4) gmap_tail_kernel<<<1, 32, 0, s>>>(I, Ig, n4 * 4, count, fidelity, gexp);
   return cudaGetLastError();
 }
 

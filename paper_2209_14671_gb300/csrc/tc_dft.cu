@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const TcArgs a) {
 }
 
 // Residual, normaliser and W on the 128 x 128 spatial tile of LED b (Eqs. 5, 12, 11; Eq. 4/10
-// for the amplitude fidelity) from o' = O'[x][y] (the transposed raw IDFT) times u^-2 n^-2.
+// for the amplitude fidelity; the Sec. 6.3 power and log maps for fidelity 2 and 3) from o' = O'[x][y] (the transposed raw IDFT) times u^-2 n^-2.
 // W' = o' f needs no (-1)^(x+y) factor: the inverse shift's sign and the forward shift's sign
 // multiply to 1.  W' goes to the image of gemm 3's B (128 rows x, K = [Re W' | Im W'] over y);
 // FP64-accurate cost partial per LED.
@@ -382,7 +382,15 @@ __global__ void __launch_bounds__(1024) tc_stencil_kernel(const TcArgs a) {
     const float2 o = Ot[p];
     const float m2 = (o.x * o.x + o.y * o.y) * (scale * scale);
     const float meas = R[y * P + x];
-    R[y * P + x] = (a.fidelity == 0) ? (m2 - meas) : (sqrtf(m2) - sqrtf(fmaxf(meas, 0.f)));
+    float r;
+    if (a.fidelity == 0) {
+      r = m2 - meas;
+    } else if (a.fidelity == 1) {
+      r = sqrtf(m2) - sqrtf(fmaxf(meas, 0.f));
+    } else {  // Sec. 6.3 maps: meas already holds g(max(I, 0))
+      r = ((a.fidelity == 2) ? powf(m2, a.gexp) : log1pf(m2)) - meas;
+    }
+    R[y * P + x] = r;
   }
   __syncthreads();
   const float tau = a.tau, tau2 = fmaxf(a.tau * a.tau, 1e-36f), hit = (a.tau > 0.f) ? 0.5f / a.tau : 0.f;
@@ -423,7 +431,9 @@ __global__ void __launch_bounds__(1024) tc_stencil_kernel(const TcArgs a) {
       const float2 o = Ot[(size_t)x * n + y];
       const float2 os = make_float2(o.x * scale, o.y * scale);
       float f = w;
-      if (a.fidelity != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(os)), a.eta));
+      if (a.fidelity == 1) f = w / (2.f * fmaxf(sqrtf(cabs2(os)), a.eta));
+      if (a.fidelity == 2) f = w * a.gexp * powf(fmaxf(cabs2(os), a.eta * a.eta), a.gexp - 1.f);
+      if (a.fidelity == 3) f = w / (cabs2(os) + 1.f);
       re[i] = os.x * f;
       im[i] = os.y * f;
     }

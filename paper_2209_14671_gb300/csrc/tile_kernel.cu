@@ -115,8 +115,10 @@ struct OmegaOut {
   float wx, wy, phi;
 };
 
-// FID: 0 = intensity fidelity (Eq. 5), 1 = amplitude (Eq. 4); ISO: 1 = isotropic normaliser,
-// 0 = anisotropic (Eq. 12).  Compile-time, so the per-pixel loops carry no untaken branch work.
+// FID: 0 = intensity fidelity (Eq. 5), 1 = amplitude (Eq. 4), 2 = a scaling map of Sec. 6.3 (power
+// or log, chosen at run time by a.fidelity = 2 or 3; meas then holds g(max(I, 0))); ISO: 1 = isotropic
+// normaliser, 0 = anisotropic (Eq. 12).  Compile-time, so the per-pixel loops carry no untaken branch
+// work in the two forms of the paper's Eqs. 4-5.
 template <int NL, int CS, int NT, int FID, int ISO>
 __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int NW = NT / 32;
@@ -290,13 +292,17 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1));
     return;  // no remote access after the last cluster barrier
   }
-  // residual r = |o|^2 - I (Eq. 5) or |o| - sqrt(max(I, 0)) (Eq. 4)
+  // residual r = |o|^2 - I (Eq. 5), |o| - sqrt(max(I, 0)) (Eq. 4) or g(|o|^2) - g(max(I, 0)) with the
+  // measured side already mapped (Sec. 6.3)
+  const bool gpow = a.fidelity == 2;
   auto resid = [&](float2 o, float meas) -> float {
     const float m2 = cabs2(o);
     if constexpr (FID == 0) {
       return m2 - meas;
-    } else {
+    } else if constexpr (FID == 1) {
       return sqrtf(m2) - sqrtf(fmaxf(meas, 0.f));
+    } else {
+      return (gpow ? powf(m2, a.gexp) : log1pf(m2)) - meas;
     }
   };
 
@@ -393,7 +399,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
           w += wy_prev;
           acc += w0.phi;
           float f = w;
-          if constexpr (FID != 0) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
+          if constexpr (FID == 1) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
+          if constexpr (FID == 2) {  // g'(|o|^2): gamma max(|o|, eta)^(2 gamma - 2), or 1 / (|o|^2 + 1)
+            const float m2 = cabs2(o_cur);
+            f = gpow ? w * a.gexp * powf(fmaxf(m2, a.eta * a.eta), a.gexp - 1.f) : w / (m2 + 1.f);
+          }
           OC[FftTeam<NL>::pidx(y) * PO + c] = cscale(o_cur, f);
         }
         wy_prev = w0.wy;
@@ -508,12 +518,15 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  const int var = (a.mode == 1) ? 1 : (a.fidelity ? 2 : 0) + (a.iso ? 1 : 0);
+  const int fid = (a.fidelity >= 2) ? 2 : a.fidelity;
+  const int var = (a.mode == 1) ? 1 : 2 * fid + (a.iso ? 1 : 0);
   switch (var) {
     case 0: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 0>, a);
     case 1: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 1>, a);
     case 2: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 1, 0>, a);
-    default: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 1, 1>, a);
+    case 3: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 1, 1>, a);
+    case 4: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 2, 0>, a);
+    default: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 2, 1>, a);
   }
 }
 
@@ -525,7 +538,7 @@ static cudaError_t prepare_tile_t(int rowsA) {
   if (smem <= configured) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (auto k : {tile_kernel<NL, CS, NT, 0, 0>, tile_kernel<NL, CS, NT, 0, 1>, tile_kernel<NL, CS, NT, 1, 0>,
-                 tile_kernel<NL, CS, NT, 1, 1>})
+                 tile_kernel<NL, CS, NT, 1, 1>, tile_kernel<NL, CS, NT, 2, 0>, tile_kernel<NL, CS, NT, 2, 1>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) configured = smem;
   return e;

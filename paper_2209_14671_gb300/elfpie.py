@@ -32,7 +32,7 @@ class ElfOptions(ctypes.Structure):
     _fields_ = [("fidelity", c_int), ("omega_iso", c_int), ("learn_pupil", c_int), ("pupil_filter", c_int),
                 ("alpha", c_double), ("beta", c_double), ("gamma1", c_double), ("gamma2", c_double),
                 ("s0_psi", c_double), ("s0_pupil", c_double), ("eta_opt", c_double), ("eta_h", c_double),
-                ("tau_fid", c_double), ("tau_h", c_double), ("tile_dft", c_int)]
+                ("tau_fid", c_double), ("tau_h", c_double), ("tile_dft", c_int), ("g_exponent", c_double)]
 
 
 class ElfState(ctypes.Structure):

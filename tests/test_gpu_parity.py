@@ -252,10 +252,12 @@ def test_device_pointers_through_torch():
 
 
 @pytest.mark.parametrize("name", ["small32", "w0", "w1"])
-@pytest.mark.parametrize("variant", [dict(fidelity=1), dict(omega_iso=0), dict(pupil_filter=0)])
+@pytest.mark.parametrize("variant", [dict(fidelity=1), dict(omega_iso=0), dict(pupil_filter=0),
+                                     dict(fidelity=2, g_exponent=0.375), dict(fidelity=3)])
 def test_option_variants_one_iteration(name, variant):
-    """Amplitude fidelity (Eqs. 4, 10, 17), anisotropic normaliser (Eq. 12 second case) and the
-    unfiltered pupil update: one iteration from the same developed state."""
+    """Amplitude fidelity (Eqs. 4, 10, 17), anisotropic normaliser (Eq. 12 second case), the
+    unfiltered pupil update and the power / log scaling maps of Sec. 6.3: one iteration from the
+    same developed state."""
     c = case(name)
     st = developed_state(name, **variant)
     I = c["I"].astype(np.float64)
@@ -268,8 +270,42 @@ def test_option_variants_one_iteration(name, variant):
         elf.step(1)
         out = elf.get_state()
         costs = elf.get_costs()[-1]
-    a_ref = O.alpha_estimate(I, amplitude=(variant.get("fidelity", 0) == 1))
+    a_ref = O.alpha_estimate(I, opt=opt)
     e = dict(alpha=abs(a_gpu - a_ref) / a_ref, psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
              cost=float(np.max(np.abs(costs - np.asarray(costs_ref)) / np.asarray(costs_ref))))
     print(name, variant, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["alpha"] < 1e-6 and e["psi"] < TOL_STATE and e["pupil"] < TOL_STATE and e["cost"] < TOL_FWD
+
+
+@pytest.mark.parametrize("name", ["single_led", "small32", "w0", "w1"])
+@pytest.mark.parametrize("variant", [dict(fidelity=2, g_exponent=0.375), dict(fidelity=2, g_exponent=1.75),
+                                     dict(fidelity=3), dict(fidelity=3, omega_iso=0)])
+def test_scaling_map_gradients_match_oracle(name, variant):
+    """Sec. 6.3 fidelities g(x) = x^gamma and ln(x + 1): cost, tile gradients G_n and the Eq. 9 /
+    Eq. 18 sums at a developed state, same bounds as the paper's two forms."""
+    c = case(name)
+    st = developed_state(name, **variant)
+    I = c["I"].astype(np.float64)
+    opt = O.Options(**variant)
+    L_fid, g_fid, g_p, tiles = O.fidelity_cost_grad(st.psi, st.pupil, I, c["geo"], opt, want_tiles=True)
+    L_A, L_P, g_h = O.hessian_cost_grad(st.psi, st.alpha, st.beta, opt)
+    with make_elf(c, **variant) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        costs, g_psi, g_pup = elf.cost_grad(st.psi.astype(np.complex64), st.pupil.astype(np.complex64))
+        G = elf.get_tile_grads()
+        sup = elf.get_support()
+    G_ref = tiles.reshape(tiles.shape[0], -1)[:, sup]
+    e = dict(L_fid=abs(costs[0] - L_fid) / L_fid, G=rel(G, G_ref), g_psi=rel(g_psi, g_fid + g_h),
+             g_p=rel(g_pup, g_p))
+    print(name, variant, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["L_fid"] < TOL_FWD and e["G"] < TOL_GRAD and e["g_psi"] < TOL_GRAD and e["g_p"] < TOL_GRAD
+
+
+def test_scaling_map_options_are_validated():
+    c = case("tiny16")
+    for bad in (dict(fidelity=4), dict(fidelity=-1), dict(fidelity=2, g_exponent=0.0),
+                dict(fidelity=2, g_exponent=9.0), dict(fidelity=2, g_exponent=float("nan"))):
+        with pytest.raises(E.ElfError) as ei:
+            make_elf(c, **bad)
+        assert ei.value.code == E.ELF_EINVAL

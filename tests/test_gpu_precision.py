@@ -98,3 +98,26 @@ def test_fifty_iterations_against_oracle(w3):
         errs[td] = (rel(s["psi"], ref.psi), rel(s["pupil"], ref.pupil))
         print(f"tile_dft={td} after 50 iterations: psi {errs[td][0]:.2e} pupil {errs[td][1]:.2e}")
     assert errs[0][0] < 3e-4 and errs[0][1] < 3e-4 and errs[1][0] < 2e-3 and errs[1][1] < 2e-3
+
+
+@pytest.mark.parametrize("variant", [dict(fidelity=2, g_exponent=0.375), dict(fidelity=3)])
+def test_tensor_core_scaling_maps_match_oracle(w3, variant):
+    """The Sec. 6.3 power and log fidelities on the tensor-core tile path: one iteration from the
+    oracle state developed under the same fidelity, against the FP64 oracle."""
+    c, _, _ = w3
+    I = c["I"].astype(np.float64)
+    opt = O.Options(**variant)
+    st = O.init_state(I, c["geo"], c["k_xy"], opt)
+    st, _ = O.run(st, I, c["geo"], opt, 3)
+    st = oracle_state_to_f32(st)
+    ref, costs_ref, _ = O.iteration(st, I, c["geo"], opt)
+    with _elf(c, 1, **variant) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        elf.step(1)
+        s = elf.get_state()
+        costs = elf.get_costs()[-1]
+    e = dict(psi=rel(s["psi"], ref.psi), pupil=rel(s["pupil"], ref.pupil),
+             cost=float(np.max(np.abs(costs - np.asarray(costs_ref)) / np.asarray(costs_ref))))
+    print(variant, "tile_dft=1 one iteration: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["psi"] < 1e-5 and e["pupil"] < 1e-5 and e["cost"] < 1e-4

@@ -30,7 +30,7 @@ def test_exports_every_declared_symbol(lib):
 def test_default_options_match_paper_defaults(lib):
     o = E.default_options()
     assert (o.gamma1, o.gamma2, o.s0_psi) == (0.9, 0.999, 1.0)
-    assert o.alpha < 0 and o.beta < 0 and o.fidelity == 0 and o.omega_iso == 1
+    assert o.alpha < 0 and o.beta < 0 and o.fidelity == 0 and o.omega_iso == 1 and o.g_exponent == 1.0
 
 
 def _create(n=64, u=4, k=((0.0, 0.0),), na=0.1, wl=0.63, dx=1.625, **opts):
