@@ -64,6 +64,9 @@ typedef struct {
   double na;              /* objective numerical aperture (> 0) */
   double wavelength_um;   /* illumination wavelength (> 0) */
   double pixel_um;        /* low-res pixel size at the sample plane (> 0) */
+  int n_mux;              /* M, LEDs lit together per measured image (Eq. 1); 0 or 1 = sequential FPM.
+                             Image j is lit by LEDs jM .. jM+M-1 (caller order); K must be a multiple
+                             of M and the measurements hold K/M images.  M > 1 needs tile_dft = 0. */
 } elf_problem;
 
 /* Hyper-parameters (Sec. 6.2) and the smoothing constants of the readings. */
@@ -110,12 +113,13 @@ int elf_default_options(elf_options* o);
  * opt may be NULL (defaults).  cuda_stream is a cudaStream_t (may be NULL). */
 int elf_create(const elf_problem* prob, const elf_options* opt, void* cuda_stream, elf_handle* out);
 
-/* Copies the K measured images I [K][n][n] float (host or device) into the
- * handle, estimates alpha = beta with Eq. 16 (Eq. 17 for the amplitude fidelity)
- * when the options ask for it, and initialises the state (reading A9 of the
- * design notes): Psi0 = u^2 * centred DFT of sqrt(max(I_c, 0)) of the LED nearest
- * the axis, Nyquist row/column zeroed, placed at that LED's window; P0 = 1 on the
- * support; mu = v = 0; delta = s0^2; t = 0.  Non-finite input -> ELF_EINVAL. */
+/* Copies the K/M measured images I [K/M][n][n] float (host or device; M = n_mux,
+ * one image per LED when M = 1) into the handle, estimates alpha = beta with
+ * Eq. 16 (Eq. 17 for the amplitude fidelity) over those images when the options
+ * ask for it, and initialises the state: Psi0 = u^2 * centred DFT of
+ * sqrt(max(I_c, 0)) of the image holding the LED nearest the axis, Nyquist
+ * row/column zeroed, placed at that LED's window; P0 = 1 on the support;
+ * mu = v = 0; delta = s0^2; t = 0.  Non-finite input -> ELF_EINVAL. */
 int elf_set_measurements(elf_handle h, const float* I, int is_device);
 
 /* Runs n_iter outer iterations of Algorithm 1 (Eqs. 9-19) asynchronously. */
@@ -143,9 +147,10 @@ int elf_set_state(elf_handle h, const elf_state* in, int is_device);
 int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs3,
                   float* g_psi, float* g_pupil, int is_device);
 
-/* Forward model of Eq. 1 for data synthesis: I_n = |o_n|^2 for every LED of the
- * handle's geometry, from the spatial object obj [N][N][2] and the unit pupil on
- * the support.  Writes I_out [K][n][n] float. */
+/* Forward model of Eq. 1 for data synthesis: I_j = sum over the M LEDs of image j
+ * of |o|^2 (|o_n|^2 per LED when M = 1) for the handle's geometry, from the spatial
+ * object obj [N][N][2] and the unit pupil on the support.  Writes I_out [K/M][n][n]
+ * float. */
 int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device);
 
 /* Inspection: the per-LED tile gradients G_n = u^-2 n^-2 fftshift(DFT_n(W_n))

@@ -51,6 +51,7 @@ int noalloc_set_error(int code, const char* msg) { return set_error(code, msg); 
 struct elf_handle_s {
   int n = 0, u = 0, N = 0, K = 0, S = 0, Blo = 0, nb = 0, rowsA = 0, cs = 1, Q = 1;
   int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;
+  int mux = 1, n_img = 0;  // LEDs per measured image (Eq. 1) and the number of images K / mux
   double dk = 0.0;
   elf_options opt{};
   cudaStream_t user = nullptr, cap = nullptr, aux = nullptr, paux = nullptr;  // paux: pupil chain
@@ -73,6 +74,11 @@ struct elf_handle_s {
   // data and state
   float* I = nullptr;
   float* Ig = nullptr;  // g(max(I, 0)) for the Sec. 6.3 scaling maps (fidelity 2, 3); else null
+  // multiplexed images (mux > 1): per-LED |o|^2, per-image residual and factor f, cost partials
+  float* Imod = nullptr;
+  float* mux_r = nullptr;
+  float* mux_f = nullptr;
+  double* mux_cost = nullptr;
   float2 *psi = nullptr, *mu_psi = nullptr;
   float *v_psi = nullptr, *delta_psi = nullptr;
   float2 *pupil = nullptr, *pupil_next = nullptr, *mu_p = nullptr;
@@ -197,6 +203,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ta.fidelity = h->opt.fidelity;
   ta.iso = h->opt.omega_iso;
   ta.mode = 0;
+  ta.mux = h->mux;
   ELF_MARK(s0, ELF_STAGE_TILE, 0);
   if (h->opt.tile_dft) {
     TcArgs tc{};
@@ -232,6 +239,20 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     tc.fidelity = ta.fidelity;
     tc.iso = ta.iso;
     ELF_CK(launch_tc_tile(tc, s0));
+  } else if (h->mux > 1) {
+    // multiplexed images: |o|^2 of every LED, per-image residual / normaliser / factor f, then
+    // W = o f per LED (mux_kernels.cu)
+    TileArgs t1 = ta;
+    t1.mode = 1;
+    t1.I_out = h->Imod;
+    ELF_CK(launch_tile(t1, h->n, s0));
+    ELF_CK(launch_mux_resid(h->Imod, ta.meas, h->mux_r, h->mux_f, h->n_img, h->mux, h->n, h->opt.fidelity, ta.gexp,
+                            ta.eta, s0));
+    ELF_CK(launch_mux_omega(h->mux_r, h->mux_f, h->mux_cost, h->n_img, h->n, ta.tau, ta.iso, s0));
+    TileArgs t2 = ta;
+    t2.mode = 2;
+    t2.meas = h->mux_f;
+    ELF_CK(launch_tile(t2, h->n, s0));
   } else {
     ELF_CK(launch_tile(ta, h->n, s0));
   }
@@ -243,10 +264,14 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_tile, 0));
   ELF_MARK(h->aux, ELF_STAGE_COST, 0);
   {
-    const bool tc = h->opt.tile_dft != 0;
-    ELF_CK(launch_cost_reduce(h->cost_fid, tc ? h->K : 0, h->cost_ff, tc ? 0 : h->K * h->cs * tile_warps(h->n),
-                              h->cost_h, h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev,
-                              mode == 1 ? h->out3 : nullptr, h->aux));
+    // fidelity partials: FP64 per LED (tensor-core path), per image block (multiplexed images), or
+    // the tile kernel's per-warp pairs
+    const bool tc = h->opt.tile_dft != 0, mx = h->mux > 1;
+    const double* fid = mx ? h->mux_cost : h->cost_fid;
+    const int nfid = tc ? h->K : (mx ? h->n_img * mux_blocks_per_image(h->n) : 0);
+    ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs * tile_warps(h->n), h->cost_h,
+                              h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out3 : nullptr,
+                              h->aux));
   }
   ELF_MARK(h->aux, ELF_STAGE_COST, 1);
   ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
@@ -459,6 +484,11 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
         std::isfinite(op.beta) && op.fidelity >= 0 && op.fidelity <= 3 && (op.tile_dft == 0 || op.tile_dft == 1) &&
         (op.fidelity != 2 || (std::isfinite(op.g_exponent) && op.g_exponent > 0 && op.g_exponent <= 8))))
     return set_error(ELF_EINVAL, "invalid options");
+  const int M = p->n_mux <= 0 ? 1 : p->n_mux;
+  if (M > K || K % M != 0) return set_error(ELF_EINVAL, "n_led must be a positive multiple of n_mux");
+  if (M > 1 && op.tile_dft) return set_error(ELF_EINVAL, "multiplexed images (n_mux > 1) need tile_dft = 0");
+  h->mux = M;
+  h->n_img = K / M;
   h->n = n;
   h->u = u;
   h->N = n * u;
@@ -571,8 +601,15 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = upload(h, &h->tile_led, tled))) return rc;
   if ((rc = upload(h, &h->tw_n, twiddles(n)))) return rc;
   if ((rc = upload(h, &h->tw_N, twiddles(N)))) return rc;
-  if ((rc = dalloc(h, &h->I, (size_t)K * B))) return rc;
-  if (op.fidelity >= 2 && (rc = dalloc(h, &h->Ig, (size_t)K * B))) return rc;
+  const size_t nI = (size_t)h->n_img * B;
+  if ((rc = dalloc(h, &h->I, nI))) return rc;
+  if (op.fidelity >= 2 && (rc = dalloc(h, &h->Ig, nI))) return rc;
+  if (M > 1) {
+    if ((rc = dalloc(h, &h->Imod, (size_t)K * B))) return rc;
+    if ((rc = dalloc(h, &h->mux_r, nI))) return rc;
+    if ((rc = dalloc(h, &h->mux_f, nI))) return rc;
+    if ((rc = dalloc(h, &h->mux_cost, (size_t)h->n_img * mux_blocks_per_image(n)))) return rc;
+  }
   if ((rc = dalloc(h, &h->psi, A))) return rc;
   if ((rc = dalloc(h, &h->mu_psi, A))) return rc;
   if ((rc = dalloc(h, &h->v_psi, A))) return rc;
@@ -653,13 +690,14 @@ int init_state_async(elf_handle h) {
   cudaStream_t s = h->user;
   // alpha = beta (Eqs. 16-17) and the initial state (reading A9)
   if (h->opt.fidelity >= 2) {  // Sec. 6.3 maps: the measured side g(max(I, 0)), also what Eq. 16 reads
-    ELF_CK(launch_gmap(h->I, h->Ig, (size_t)h->K * B, h->opt.fidelity, (float)h->opt.g_exponent, s));
-    ELF_CK(launch_alpha(h->Ig, h->K, h->n, 0, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
+    ELF_CK(launch_gmap(h->I, h->Ig, (size_t)h->n_img * B, h->opt.fidelity, (float)h->opt.g_exponent, s));
+    ELF_CK(launch_alpha(h->Ig, h->n_img, h->n, 0, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
   } else {
-    ELF_CK(launch_alpha(h->I, h->K, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha,
+    ELF_CK(launch_alpha(h->I, h->n_img, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha,
                         h->opt.beta, s));
   }
-  ELF_CK(launch_init_small(h->I + (size_t)h->centre * B, h->small, h->n, s));
+  // Psi0 from the image that holds the centre LED (its own image when mux = 1)
+  ELF_CK(launch_init_small(h->I + (size_t)(h->centre / h->mux) * B, h->small, h->n, s));
   ELF_CK(launch_fft2(h->small, h->n, false, h->tw_n, s));
   ELF_CK(launch_embed(h->small, h->psi, h->n, h->N, h->origin_h[h->centre].x, h->origin_h[h->centre].y,
                       (float)(h->u * h->u), s));
@@ -678,7 +716,7 @@ int init_state_async(elf_handle h) {
 
 // Asynchronous job pieces for the serving scheduler (server.cu).
 int handle_set_measurements_async(elf_handle h, const float* I) {
-  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * h->n * h->n * sizeof(float), cudaMemcpyDefault, h->user));
+  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->n_img * h->n * h->n * sizeof(float), cudaMemcpyDefault, h->user));
   return init_state_async(h);
 }
 
@@ -709,9 +747,9 @@ extern "C" int elf_set_measurements(elf_handle h, const float* I, int is_device)
   (void)is_device;
   const size_t B = (size_t)h->n * h->n;
   cudaStream_t s = h->user;
-  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->K * B * sizeof(float), cudaMemcpyDefault, s));
+  ELF_CK(cudaMemcpyAsync(h->I, I, (size_t)h->n_img * B * sizeof(float), cudaMemcpyDefault, s));
   ELF_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
-  ELF_CK(launch_count_nonfinite(h->I, (size_t)h->K * B, h->flag, s));
+  ELF_CK(launch_count_nonfinite(h->I, (size_t)h->n_img * B, h->flag, s));
   int bad = 0;
   ELF_CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   ELF_CK(cudaStreamSynchronize(s));
@@ -876,10 +914,11 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   ELF_CK(cudaMemcpyAsync(h->psi_eval, obj, A * 8, cudaMemcpyDefault, s));
   ELF_CK(launch_sign_scale(h->psi_eval, h->psi_eval, h->N, 1.f, s));
   ELF_CK(launch_fft2(h->psi_eval, h->N, false, h->tw_N, s));
+  const size_t nI = (size_t)h->n_img * B;  // K/M images of Eq. 1
   float* dst = I_out;
   float* staging = nullptr;
   if (!is_device) {
-    ELF_CK(cudaMalloc(&staging, (size_t)h->K * B * sizeof(float)));
+    ELF_CK(cudaMalloc(&staging, nI * sizeof(float)));
     dst = staging;
   }
   TileArgs ta{};
@@ -890,7 +929,7 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   ta.row_cnt = h->row_cnt;
   ta.row_off = h->row_off;
   ta.tw = h->tw_n;
-  ta.I_out = dst;
+  ta.I_out = h->mux > 1 ? h->Imod : dst;  // per-LED |o|^2, summed per image below when M > 1
   ta.cost_ff = h->cost_ff;
   ta.err = h->tc_err;
   ta.N = h->N;
@@ -901,8 +940,10 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   ta.rowsA = h->rowsA;
   ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
   ta.mode = 1;
+  ta.mux = h->mux;
   cudaError_t e = launch_tile(ta, h->n, s);
-  if (e == cudaSuccess && staging) e = cudaMemcpyAsync(I_out, staging, (size_t)h->K * B * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && h->mux > 1) e = launch_mux_sum(h->Imod, dst, h->n_img, h->mux, h->n, s);
+  if (e == cudaSuccess && staging) e = cudaMemcpyAsync(I_out, staging, nI * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (staging) cudaFree(staging);
   if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("elf_simulate: ") + cudaGetErrorString(e));

@@ -30,13 +30,23 @@ struct TileArgs {
   float tau, eta;
   float gexp;             // gamma of the power map (fidelity 2)
   int fidelity, iso;      // fidelity 2 and 3 read meas = g(max(I, 0)) (Sec. 6.3)
-  int mode;               // 0 = gradient, 1 = simulate |o|^2
+  int mode;               // 0 = gradient, 1 = simulate |o|^2, 2 = gradient of multiplexed images:
+                          // meas holds the per-image factor f (mux_kernels.cu), W = o f
+  int mux;                // M: LEDs per image; LED k reads image k / M in mode 2
 };
 int tile_cluster_size(int n);
 int tile_warps(int n);                        // warps per CTA of the tile kernel
 size_t tile_smem_bytes(int n, int cs, int rowsA);
 cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
 cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------- multiplexed images (mux_kernels.cu)
+int mux_blocks_per_image(int n);  // cost partials per image of mux_omega
+cudaError_t launch_mux_resid(const float* Imod, const float* meas, float* R, float* F, int n_img, int M, int n,
+                             int fidelity, float gexp, float eta, cudaStream_t s);
+cudaError_t launch_mux_omega(const float* R, float* F, double* partial, int n_img, int n, float tau, int iso,
+                             cudaStream_t s);
+cudaError_t launch_mux_sum(const float* Imod, float* out, int n_img, int M, int n, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core tile path (tc_dft.cu)
 constexpr int kTcN = 128;     // tile side of the tensor-core path

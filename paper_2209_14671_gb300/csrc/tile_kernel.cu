@@ -147,6 +147,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const int team = tid / TL;
   const int x0 = crank * CW;
   const size_t img = (size_t)led * NL * NL;
+  // mode 2 (multiplexed images) reads the factor f of the LED's image j = led / M in place of I
+  const size_t meas_img = (size_t)(a.mode == 2 ? led / a.mux : led) * NL * NL;
+  const bool has_meas = a.mode != 1;
 
   // twiddles (group 0) and this CTA's columns of I_n (group 1, overlapping stages A and B)
   // arrive by cp.async in 16-byte chunks
@@ -157,16 +160,16 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
                    : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  if (a.mode == 0) {
+  if (has_meas) {
     constexpr int CH = CW / 4;  // 16-byte chunks per row
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(Itile);
     for (int i = tid; i < NL * CH; i += NT) {
       const int y = i / CH, k = i - y * CH;
-      const float* src = a.meas + img + (size_t)y * NL + x0 + 4 * k;
+      const float* src = a.meas + meas_img + (size_t)y * NL + x0 + 4 * k;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 4u * (y * CW + 4 * k)), "l"(src)
                    : "memory");
     }
-    for (int i = tid; i < 2 * NL; i += NT) {
+    for (int i = tid; i < (a.mode == 0 ? 2 * NL : 0); i += NT) {  // halo columns: mode 0 only
       const int side = i / NL, y = i - side * NL;
       const int x = side ? x0 + CW : x0 - 1;
       if (x < 0 || x >= NL) continue;
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
     }
     if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
-      if (a.mode == 0) {
+      if (has_meas) {
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
       } else {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     const bool act = (lc < WC) && x >= 0 && x < NL;
     team_fft<NL, true, PO>(OC + (act ? lc : 0), tw, lane, act, a.Blo, a.nb);
   }
-  if (a.mode == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (has_meas) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
   // o = (-1)^(x+y) scale * IDFT.  The stencil only needs |o| and W = o w times the same
@@ -314,7 +317,14 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // halo columns are evaluated by the edge lanes.  The rows just outside the strip
   // are read before a block barrier, because their owners overwrite them with W.
   float acc = 0.f;  // per-thread partial of at most NL/SW pixels; block sum in FP64
-  {
+  if (a.mode == 2) {
+    // multiplexed images: W = o f, with f = g'(s_j) nabla^T omega of the LED's image computed once
+    // per image beforehand (residual, normaliser and cost are per image, not per LED)
+    for (int i = tid; i < NL * CW; i += NT) {
+      const int y = i / CW, cc = i - y * CW;
+      OC[FftTeam<NL>::pidx(y) * PO + cc + 1] = cscale(load_o(y, cc + 1), Itile[y * CW + cc]);
+    }
+  } else {
     static_assert(CW <= 32, "one warp spans the owned columns");
     constexpr int SW = pow2_floor(NW);  // strip warps; the others only take part in the barrier
     constexpr int RPW = NL / SW;        // rows per strip
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         r_cur = r_nxt;
       }
     }
-  }
+  }  // mode 2 leaves acc = 0: the cost pairs of its LEDs are zero
   // the warp's cost pair, summed in a fixed order with the other warps' by the cost reduction
   {
     const FF wsum = warp_sum_ff(FF{acc, 0.f});
@@ -519,7 +529,7 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     cfg.numAttrs = 1;
   }
   const int fid = (a.fidelity >= 2) ? 2 : a.fidelity;
-  const int var = (a.mode == 1) ? 1 : 2 * fid + (a.iso ? 1 : 0);
+  const int var = (a.mode != 0) ? 1 : 2 * fid + (a.iso ? 1 : 0);  // modes 1, 2 skip the stencil
   switch (var) {
     case 0: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 0>, a);
     case 1: return cudaLaunchKernelEx(&cfg, tile_kernel<NL, CS, NT, 0, 1>, a);

@@ -25,7 +25,7 @@ P_float, P_double, P_int = ctypes.POINTER(c_float), ctypes.POINTER(c_double), ct
 
 class ElfProblem(ctypes.Structure):
     _fields_ = [("n_lowres", c_int), ("upsample", c_int), ("n_led", c_int), ("k_xy", P_float),
-                ("na", c_double), ("wavelength_um", c_double), ("pixel_um", c_double)]
+                ("na", c_double), ("wavelength_um", c_double), ("pixel_um", c_double), ("n_mux", c_int)]
 
 
 class ElfOptions(ctypes.Structure):
@@ -145,12 +145,12 @@ def _stream_handle(stream) -> int:
 class Elf:
     """One reconstruction problem held on the GPU (an ``elf_handle``)."""
 
-    def __init__(self, n, upsample, k_xy, na, wavelength_um, pixel_um, options=None, stream=None):
+    def __init__(self, n, upsample, k_xy, na, wavelength_um, pixel_um, options=None, stream=None, mux=1):
         lib = load()
         k = np.ascontiguousarray(np.asarray(k_xy, dtype=np.float32).reshape(-1, 2))
         self._k = k
         prob = ElfProblem(int(n), int(upsample), int(k.shape[0]), k.ctypes.data_as(P_float),
-                          float(na), float(wavelength_um), float(pixel_um))
+                          float(na), float(wavelength_um), float(pixel_um), int(mux))
         if options is None:
             options = default_options()
         elif isinstance(options, dict):
@@ -161,6 +161,8 @@ class Elf:
                               ctypes.byref(h)), "elf_create")
         self._h = h
         self.n, self.u, self.K = int(n), int(upsample), int(k.shape[0])
+        self.mux = int(mux) if int(mux) > 0 else 1
+        self.n_img = self.K // self.mux  # measured images (Eq. 1)
         self.N = self.n * self.u
         self.S = _check(lib.elf_get_support(self._h, None), "elf_get_support")
 
@@ -282,9 +284,10 @@ class Elf:
         return _check(load().elf_graph_kernel_count(self._h), "elf_graph_kernel_count")
 
     def simulate(self, obj, out=None):
-        """Predicted intensities |o_n|^2 [K, n, n] float32 of the spatial object ``obj``."""
+        """Predicted intensities of Eq. 1 [K/M, n, n] float32 of the spatial object ``obj``
+        (|o_n|^2 per LED when M = 1, the sum over each image's M LEDs otherwise)."""
         if out is None:
-            out = np.empty((self.K, self.n, self.n), np.float32)
+            out = np.empty((self.n_img, self.n, self.n), np.float32)
         po, dev = _ptr(obj)
         pi, dev2 = _ptr(out)
         _check(load().elf_simulate(self._h, c_void_p(po), c_void_p(pi), dev2), "elf_simulate")
