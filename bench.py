@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision leg")
     ap.add_argument("--no-fidelity", action="store_true", help="skip the fidelity-variant leg")
+    ap.add_argument("--no-mux", action="store_true", help="skip the multiplexed-illumination leg")
     ap.add_argument("--serving-requests", type=int, default=120,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
@@ -296,6 +297,38 @@ def fidelity_leg(w, I_dev, torch, dev):
             "note": "traced steps (CUDA events inside the graph); parity: tests/test_gpu_parity.py"}
 
 
+def mux_leg(wid, w, obj_dev, torch, dev):
+    """Multiplexed illumination (Eq. 1): the benchmark workload's 225 LEDs lit 5 at a time
+    (45 images, LEDs 5j .. 5j+4 per image), measurements from the GPU's multiplexed forward
+    model plus the workload's seeded Gaussian noise level of 1e-3.  Median iteration and tile
+    stage (|o|^2 pass, per-image residual and normaliser, W = o f pass) over 10 traced steps."""
+    from paper_2209_14671_gb300 import elfpie as E
+    M = 5
+    stream = torch.cuda.current_stream(dev)
+    elf = E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"], stream=stream, mux=M)
+    I = torch.empty((w["K"] // M, w["n"], w["n"]), dtype=torch.float32, device=dev)
+    elf.simulate(obj_dev, I)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    I += 1e-3 * torch.randn(I.shape, generator=g, device=dev)
+    elf.set_measurements(I)
+    elf.set_tracing(True)
+    for _ in range(3):
+        elf.step(1)
+    t_it, t_tile = [], []
+    for _ in range(10):
+        elf.step(1)
+        st = elf.stage_times()
+        t_it.append(st["iteration"])
+        t_tile.append(st["tile"])
+    elf.close()
+    it = float(np.median(t_it))
+    return {"workload": f"{w['name']}_mux{M}", "leds_per_image": M, "images": w["K"] // M,
+            "iteration_ms": it, "tile_stage_ms": float(np.median(t_tile)),
+            "led_updates_per_s": w["K"] / (it * 1e-3),
+            "note": "traced steps; parity: tests/test_gpu_mux.py"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -441,6 +474,11 @@ def run_ours(args):
     if not args.no_fidelity and world == 1:
         fidelity = fidelity_leg(w, I_dev, torch, dev)
 
+    mux = None
+    if not args.no_mux and world == 1:
+        obj = torch.from_numpy(IN.object_field(wid, w).astype(np.complex64)).to(dev)
+        mux = mux_leg(wid, w, obj, torch, dev)
+
     serving = None
     if args.serving_requests > 0:
         serving = serving_leg(args, torch, dev)
@@ -477,6 +515,7 @@ def run_ours(args):
             "serving": serving,
             "precision": precision,
             "fidelity_variants": fidelity,
+            "multiplexed": mux,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -73,7 +73,7 @@ struct elf_handle_s {
   float2 *tw_n = nullptr, *tw_N = nullptr;
   // data and state
   float* I = nullptr;
-  float* Ig = nullptr;  // g(max(I, 0)) for the Sec. 6.3 scaling maps (fidelity 2, 3); else null
+  float* Ig = nullptr;  // g(max(I, 0)): sqrt (fidelity 1) or a Sec. 6.3 map (2, 3); null for fidelity 0
   // multiplexed images (mux > 1): per-LED |o|^2, per-image residual and factor f, cost partials
   float* Imod = nullptr;
   float* mux_r = nullptr;
@@ -180,7 +180,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   TileArgs ta{};
   ta.psi = psi;
   ta.pupil = pupil;
-  ta.meas = h->opt.fidelity >= 2 ? h->Ig : h->I;
+  ta.meas = h->opt.fidelity >= 1 ? h->Ig : h->I;
   ta.origin = h->origin;
   ta.row_xs = h->row_xs;
   ta.row_cnt = h->row_cnt;
@@ -603,7 +603,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = upload(h, &h->tw_N, twiddles(N)))) return rc;
   const size_t nI = (size_t)h->n_img * B;
   if ((rc = dalloc(h, &h->I, nI))) return rc;
-  if (op.fidelity >= 2 && (rc = dalloc(h, &h->Ig, nI))) return rc;
+  if (op.fidelity >= 1 && (rc = dalloc(h, &h->Ig, nI))) return rc;
   if (M > 1) {
     if ((rc = dalloc(h, &h->Imod, (size_t)K * B))) return rc;
     if ((rc = dalloc(h, &h->mux_r, nI))) return rc;
@@ -689,12 +689,11 @@ int init_state_async(elf_handle h) {
   const size_t B = (size_t)h->n * h->n, A = (size_t)h->N * h->N;
   cudaStream_t s = h->user;
   // alpha = beta (Eqs. 16-17) and the initial state (reading A9)
-  if (h->opt.fidelity >= 2) {  // Sec. 6.3 maps: the measured side g(max(I, 0)), also what Eq. 16 reads
+  if (h->opt.fidelity >= 1) {  // the measured side g(max(I, 0)), also what Eqs. 16-17 read
     ELF_CK(launch_gmap(h->I, h->Ig, (size_t)h->n_img * B, h->opt.fidelity, (float)h->opt.g_exponent, s));
     ELF_CK(launch_alpha(h->Ig, h->n_img, h->n, 0, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
   } else {
-    ELF_CK(launch_alpha(h->I, h->n_img, h->n, h->opt.fidelity == 1, h->alpha_part, h->weights, h->opt.alpha,
-                        h->opt.beta, s));
+    ELF_CK(launch_alpha(h->I, h->n_img, h->n, 0, h->alpha_part, h->weights, h->opt.alpha, h->opt.beta, s));
   }
   // Psi0 from the image that holds the centre LED (its own image when mux = 1)
   ELF_CK(launch_init_small(h->I + (size_t)(h->centre / h->mux) * B, h->small, h->n, s));

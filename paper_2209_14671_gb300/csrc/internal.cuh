@@ -29,7 +29,7 @@ struct TileArgs {
   float scale;            // 1 / (u^2 n^2)
   float tau, eta;
   float gexp;             // gamma of the power map (fidelity 2)
-  int fidelity, iso;      // fidelity 2 and 3 read meas = g(max(I, 0)) (Sec. 6.3)
+  int fidelity, iso;      // fidelity 1-3 read meas = g(max(I, 0)): sqrt (Eq. 4) or a Sec. 6.3 map
   int mode;               // 0 = gradient, 1 = simulate |o|^2, 2 = gradient of multiplexed images:
                           // meas holds the per-image factor f (mux_kernels.cu), W = o f
   int mux;                // M: LEDs per image; LED k reads image k / M in mode 2
@@ -68,7 +68,7 @@ struct TcArgs {
   int* err;             // set when a bounded wait runs out
   int n, N, K, S, Blo, nb;
   float scale, tau, eta, gexp;
-  int fidelity, iso;      // fidelity 2 and 3 read meas = g(max(I, 0)) (Sec. 6.3)
+  int fidelity, iso;      // fidelity 1-3 read meas = g(max(I, 0)): sqrt (Eq. 4) or a Sec. 6.3 map
 };
 // Constant operand images, built on the host in FP64 and split into BF16 hi + lo:
 // 0 = gemm 1's two A, 1 = gemm 2's B, 2 = gemm 3's two A, 3 = gemm 4's B.
@@ -150,7 +150,8 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,
                          double fixed_alpha, double fixed_beta, cudaStream_t s);
-// Ig = g(max(I, 0)) for the Sec. 6.3 scaling maps (fidelity 2: x^gexp, 3: ln(x + 1))
+// Ig = g(max(I, 0)), the measured side of the residual (fidelity 1: sqrt, Eq. 4; 2: x^gexp, 3: ln(x + 1),
+// Sec. 6.3)
 cudaError_t launch_gmap(const float* I, float* Ig, size_t count, int fidelity, float gexp, cudaStream_t s);
 cudaError_t launch_init_small(const float* I_c, float2* small, int n, cudaStream_t s);
 cudaError_t launch_embed(const float2* small, float2* psi, int n, int N, int oy, int ox, float gain,

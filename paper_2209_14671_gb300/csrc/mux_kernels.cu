@@ -24,7 +24,7 @@ namespace elf {
 namespace {
 
 // r and g'(s) of one pixel for the model intensity s and the measured value meas (the
-// measurement itself for fidelity 0 and 1, the mapped g(max(I, 0)) for 2 and 3)
+// measurement itself for fidelity 0, the mapped g(max(I, 0)) for 1, 2 and 3)
 __device__ __forceinline__ void resid_slope(float s, float meas, int fidelity, float gexp, float eta, float& r,
                                             float& slope) {
   if (fidelity == 0) {  // Eq. 5: r = s - I, dr/ds = 1
@@ -32,7 +32,7 @@ __device__ __forceinline__ void resid_slope(float s, float meas, int fidelity, f
     slope = 1.f;
   } else if (fidelity == 1) {  // Eq. 4: r = sqrt(s) - sqrt(max(I, 0)), g' = 1 / (2 max(sqrt(s), eta))
     const float a = sqrtf(s);
-    r = a - sqrtf(fmaxf(meas, 0.f));
+    r = a - meas;  // meas holds sqrt(max(I, 0))
     slope = 1.f / (2.f * fmaxf(a, eta));
   } else if (fidelity == 2) {  // Sec. 6.3 power map
     r = powf(s, gexp) - meas;

@@ -87,8 +87,8 @@ size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity) {
   const size_t tc = tile_dft ? K * (elf::kTcImgX + elf::kTcImgY + elf::kTcImgW + elf::kTcImgZ +
                                     8 * (size_t)elf::kTcN * elf::kTcN) + (640u << 10)
                              : 0;
-  // the Sec. 6.3 scaling maps keep a mapped copy of the measurements
-  const size_t gmap = fidelity >= 2 ? 4 * nI * B : 0;
+  // the amplitude fidelity and the Sec. 6.3 maps keep a mapped copy of the measurements
+  const size_t gmap = fidelity >= 1 ? 4 * nI * B : 0;
   // multiplexed images: per-LED |o|^2, per-image residual and factor, per-block cost partials
   const size_t mux = M > 1 ? 4 * K * B + 8 * nI * B + 8 * nI * (size_t)elf::mux_blocks_per_image((int)n) : 0;
   return 8 * A * 6 + 4 * A * 2 + 4 * nI * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + gmap +

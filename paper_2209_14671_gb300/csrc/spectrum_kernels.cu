@@ -511,7 +511,8 @@ cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* pa
 }
 
 // ------------------------------------------------------------------ Sec. 6.3 scaling maps
-// The measured side of the residual g(|o|^2) - g(max(I, 0)), mapped once per set of measurements.
+// The measured side of the residual g(|o|^2) - g(max(I, 0)) of Eq. 4 (g = sqrt) and of the Sec. 6.3
+// maps, mapped once per set of measurements.
 __global__ void gmap_kernel(const float4* __restrict__ I, float4* __restrict__ Ig, size_t n4, int fidelity,
                             float gexp) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
@@ -520,7 +521,7 @@ __global__ void gmap_kernel(const float4* __restrict__ I, float4* __restrict__ I
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float x = fmaxf(e[j], 0.f);
-      e[j] = (fidelity == 2) ? powf(x, gexp) : log1pf(x);
+      e[j] = (fidelity == 1) ? sqrtf(x) : (fidelity == 2) ? powf(x, gexp) : log1pf(x);
     }
     Ig[i] = v;
   }
@@ -530,7 +531,7 @@ __global__ void gmap_tail_kernel(const float* I, float* Ig, size_t b, size_t cou
   const size_t i = b + threadIdx.x;
   if (i >= count) return;
   const float x = fmaxf(I[i], 0.f);
-  Ig[i] = (fidelity == 2) ? powf(x, gexp) : log1pf(x);
+  Ig[i] = (fidelity == 1) ? sqrtf(x) : (fidelity == 2) ? powf(x, gexp) : log1pf(x);
 }
 
 cudaError_t launch_gmap(const float* I, float* Ig, size_t count, int fidelity, float gexp, cudaStream_t s) {

@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(1024) tc_stencil_kernel(const TcArgs a) {
     if (a.fidelity == 0) {
       r = m2 - meas;
     } else if (a.fidelity == 1) {
-      r = sqrtf(m2) - sqrtf(fmaxf(meas, 0.f));
+      r = sqrtf(m2) - meas;  // meas holds sqrt(max(I, 0))
     } else {  // Sec. 6.3 maps: meas already holds g(max(I, 0))
       r = ((a.fidelity == 2) ? powf(m2, a.gexp) : log1pf(m2)) - meas;
     }

@@ -115,8 +115,8 @@ struct OmegaOut {
   float wx, wy, phi;
 };
 
-// FID: 0 = intensity fidelity (Eq. 5), 1 = amplitude (Eq. 4), 2 = a scaling map of Sec. 6.3 (power
-// or log, chosen at run time by a.fidelity = 2 or 3; meas then holds g(max(I, 0))); ISO: 1 = isotropic
+// FID: 0 = intensity fidelity (Eq. 5), 1 = amplitude (Eq. 4; meas holds sqrt(max(I, 0))), 2 = a scaling
+// map of Sec. 6.3 (power or log, chosen at run time by a.fidelity = 2 or 3; meas holds g(max(I, 0))); ISO: 1 = isotropic
 // normaliser, 0 = anisotropic (Eq. 12).  Compile-time, so the per-pixel loops carry no untaken branch
 // work in the two forms of the paper's Eqs. 4-5.
 template <int NL, int CS, int NT, int FID, int ISO>
@@ -295,18 +295,31 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1));
     return;  // no remote access after the last cluster barrier
   }
-  // residual r = |o|^2 - I (Eq. 5), |o| - sqrt(max(I, 0)) (Eq. 4) or g(|o|^2) - g(max(I, 0)) with the
-  // measured side already mapped (Sec. 6.3)
+  // residual r = |o|^2 - I (Eq. 5), |o| - sqrt(max(I, 0)) (Eq. 4) or g(|o|^2) - g(max(I, 0)) (Sec. 6.3),
+  // the measured side of Eq. 4 and of the maps mapped once per data set.  For the maps, sl = g'(|o|^2)
+  // comes out of the same evaluation: the power map as p = max(|o|^2, eta^2)^(gamma - 1), g = |o|^2 p,
+  // g' = gamma p (one powf per pixel); the log map as ln(1 + |o|^2) and 1 / (1 + |o|^2).
   const bool gpow = a.fidelity == 2;
-  auto resid = [&](float2 o, float meas) -> float {
+  const float eta2 = a.eta * a.eta;
+  auto resid_sl = [&](float2 o, float meas, float& sl) -> float {
     const float m2 = cabs2(o);
     if constexpr (FID == 0) {
       return m2 - meas;
     } else if constexpr (FID == 1) {
-      return sqrtf(m2) - sqrtf(fmaxf(meas, 0.f));
+      return sqrtf(m2) - meas;
     } else {
-      return (gpow ? powf(m2, a.gexp) : log1pf(m2)) - meas;
+      if (gpow) {
+        const float p = powf(fmaxf(m2, eta2), a.gexp - 1.f);
+        sl = a.gexp * p;
+        return m2 * p - meas;
+      }
+      sl = 1.f / (m2 + 1.f);
+      return log1pf(m2) - meas;
     }
+  };
+  auto resid = [&](float2 o, float meas) -> float {
+    float sl;
+    return resid_sl(o, meas, sl);
   };
 
   // W = o * nabla^T omega (Eq. 11) or o / (2 max(|o|, eta)) * nabla^T omega (Eq. 10),
@@ -373,7 +386,8 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     __syncthreads();
     if (strip) {
       float2 o_cur = load_o(ybeg, c);
-      float r_cur = resid(o_cur, Itile[ybeg * CW + cc]);
+      float sl_cur = 0.f, sl_nxt = 0.f;  // g'(|o|^2) of the current and next rows (Sec. 6.3 maps)
+      float r_cur = resid_sl(o_cur, Itile[ybeg * CW + cc], sl_cur);
       // omega_y at the row above the strip (0 above the first row)
       float wy_prev = 0.f;
       if (ybeg >= 1) {
@@ -391,7 +405,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         float r_nxt;
         if (i + 1 < RPW) {
           o_nxt = load_o(y + 1, c);
-          r_nxt = resid(o_nxt, Itile[(y + 1) * CW + cc]);
+          r_nxt = resid_sl(o_nxt, Itile[(y + 1) * CW + cc], sl_nxt);
         } else {
           o_nxt = o_cur;
           r_nxt = (yend < NL) ? r_below : r_cur;
@@ -409,14 +423,12 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
           w += wy_prev;
           acc += w0.phi;
           float f = w;
-          if constexpr (FID == 1) f = w / (2.f * fmaxf(sqrtf(cabs2(o_cur)), a.eta));
-          if constexpr (FID == 2) {  // g'(|o|^2): gamma max(|o|, eta)^(2 gamma - 2), or 1 / (|o|^2 + 1)
-            const float m2 = cabs2(o_cur);
-            f = gpow ? w * a.gexp * powf(fmaxf(m2, a.eta * a.eta), a.gexp - 1.f) : w / (m2 + 1.f);
-          }
+          if constexpr (FID == 1) f = w * (0.5f * rsqrtf(fmaxf(cabs2(o_cur), eta2)));  // 1 / (2 max(|o|, eta))
+          if constexpr (FID == 2) f = w * sl_cur;
           OC[FftTeam<NL>::pidx(y) * PO + c] = cscale(o_cur, f);
         }
         wy_prev = w0.wy;
+        sl_cur = sl_nxt;
         o_cur = o_nxt;
         r_cur = r_nxt;
       }
