@@ -26,6 +26,10 @@ design notes of the repository.  In short:
 * A18 multiplexing (Eq. 1 with M > 1): LEDs in the caller's order, image j is
       lit by LEDs jM .. jM+M-1 (K a multiple of M); the residual of image j
       uses sum_m |o_{j,m}|^2; Psi0 comes from the image holding the centre LED.
+* A19 Eq. 20's G (x) zeta: G = exp(-2 r^2 / w^2), w the "half-waist" read as the
+      1/e^2 radius; the blurred field min-max normalised to [0, 1] per image so
+      that c sets the illumination range [1 - c, 1].
+* A20 that convolution is circular on the n x n image grid.
 * A17 gamma / log fidelity (Sec. 6.3): g(x) = x^gamma or ln(x + 1) replaces
       the identity (Eq. 5) or sqrt (Eq. 4) map of Eq. 3; measured intensities
       are clamped at 0 before the map, and the slope g'(|o|^2) of the power map
@@ -53,7 +57,8 @@ __all__ = [
     "hessian_cost_grad", "adabelief", "gauss3", "filter3", "alpha_estimate",
     "scaling_map", "scaling_map_slope",
     "init_state", "iteration", "run", "total_cost", "centre_led",
-    "LAPLACE_KERNEL",
+    "LAPLACE_KERNEL", "gaussian_kernel_periodic", "circular_convolve", "illumination_pattern",
+    "degrade", "darkfield_images", "noise_level", "lsnr", "object_quality",
 ]
 
 
@@ -569,3 +574,97 @@ def total_cost(costs, alpha, beta):
     """Eq. 8: L = L_fid + alpha L_A + beta L_Phi."""
     c = np.asarray(costs, dtype=np.float64)
     return c[..., 0] + alpha * c[..., 1] + beta * c[..., 2]
+
+
+# ----------------------------------------------------------------------------
+# evaluation of Sec. 4.1: degradations (Eqs. 2, 20), NL (Eq. 21), LSNR (Eq. 22)
+# ----------------------------------------------------------------------------
+def gaussian_kernel_periodic(n, waist_px):
+    """G of Eq. 20 on an n x n periodic grid: exp(-2 r^2 / w^2) (w the 1/e^2 half-waist,
+    A19), r the wrapped distance to pixel (0, 0), normalised to unit sum."""
+    d = np.minimum(np.arange(n), n - np.arange(n)).astype(np.float64)
+    r2 = d[None, :] ** 2 + d[:, None] ** 2
+    g = np.exp(-2.0 * r2 / float(waist_px) ** 2)
+    return g / g.sum()
+
+
+def circular_convolve(f, g):
+    """(g (x) f)[y, x] = sum_{a, b} g[a, b] f[(y - a) mod n, (x - b) mod n], summed directly."""
+    n = f.shape[0]
+    out = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            if g[a, b] != 0.0:
+                out += g[a, b] * np.roll(np.roll(f, a, axis=0), b, axis=1)
+    return out
+
+
+def illumination_pattern(zeta, c, waist_px):
+    """Uneven illumination of Eq. 20 for one image: (1 - c) + c * N(G (x) zeta), with N the
+    min-max normalisation to [0, 1] (A19; N = 0 for a flat field) and (x) the circular
+    convolution (A20)."""
+    blur = circular_convolve(np.asarray(zeta, dtype=np.float64), gaussian_kernel_periodic(zeta.shape[0], waist_px))
+    lo, hi = blur.min(), blur.max()
+    norm = (blur - lo) / (hi - lo) if hi > lo else np.zeros_like(blur)
+    return (1.0 - c) + c * norm
+
+
+def degrade(I_clean, c=0.0, waist_px=15.0, zeta=None, background=None, gauss_a=0.0, xi=None,
+            snp_density=0.0, u_snp=None):
+    """Eqs. 2 and 20 with the random fields given: per image j,
+      I_j = Lambda_j o I_clean_j + Omega_j + a xi_j,  Lambda_j = illumination_pattern(zeta_j)
+    (Lambda = 1 when c = 0, Omega = 0 when background is None), then salt & pepper with the
+    uniform field u: u < d/2 -> 0, d/2 <= u < d -> 1 (the 'salt & pepper' rule of the
+    imnoise call of Sec. 4.1).  Arrays [K/M, n, n]; background [K/M]."""
+    I = np.array(I_clean, dtype=np.float64, copy=True)
+    for j in range(I.shape[0]):
+        if c != 0.0:
+            I[j] *= illumination_pattern(zeta[j], c, waist_px)
+        if background is not None:
+            I[j] += float(background[j])
+        if gauss_a != 0.0:
+            I[j] += gauss_a * np.asarray(xi[j], dtype=np.float64)
+    if snp_density != 0.0:
+        u = np.asarray(u_snp, dtype=np.float64)
+        I = np.where(u < snp_density / 2.0, 0.0, np.where(u < snp_density, 1.0, I))
+    return I
+
+
+def darkfield_images(geo: Geometry, na, wavelength_um):
+    """Dark-field images of Eq. 21: image j when every LED lighting it has its illumination
+    frequency outside the pupil, |c_n| dk > NA / lambda."""
+    r = np.sqrt(np.sum(geo.offsets.astype(np.float64) ** 2, axis=1)) * geo.dk
+    dark_led = r > float(na) / float(wavelength_um)
+    return dark_led.reshape(geo.n_images, geo.mux).all(axis=1)
+
+
+def noise_level(I_simu, I_noised, dark):
+    """NL of Eq. 21 in percent: mean over the dark-field images of
+    ||I_simu - I_noised||_1 / ||I_simu||_1."""
+    I_simu = np.asarray(I_simu, dtype=np.float64)
+    I_noised = np.asarray(I_noised, dtype=np.float64)
+    idx = np.flatnonzero(np.asarray(dark))
+    if idx.size == 0:
+        return 0.0
+    ratios = [np.sum(np.abs(I_simu[j] - I_noised[j])) / np.sum(np.abs(I_simu[j])) for j in idx]
+    return 100.0 * float(np.mean(ratios))
+
+
+def lsnr(rec, truth):
+    """LSNR of Eq. 22 in dB: max over b of 10 log10(||truth||^2 / ||truth - (rec + b)||^2);
+    the maximising b is the mean of truth - rec (least squares in one constant)."""
+    t = np.asarray(truth, dtype=np.float64).ravel()
+    d = t - np.asarray(rec, dtype=np.float64).ravel()
+    b = d.mean()
+    return 10.0 * math.log10(float(np.sum(t * t)) / float(np.sum((d - b) ** 2)))
+
+
+def object_quality(obj_rec, obj_true):
+    """(LSNR of the amplitude, LSNR of the phase) of a reconstruction against the truth, after
+    removing the unobservable global phase: obj_rec is multiplied by e^{i phi0} with
+    phi0 = arg sum conj(obj_rec) obj_true (the least-squares global phase)."""
+    obj_rec = np.asarray(obj_rec, dtype=np.complex128)
+    obj_true = np.asarray(obj_true, dtype=np.complex128)
+    phi0 = np.angle(np.sum(np.conj(obj_rec) * obj_true))
+    aligned = obj_rec * np.exp(1j * phi0)
+    return lsnr(np.abs(aligned), np.abs(obj_true)), lsnr(np.angle(aligned), np.angle(obj_true))

@@ -538,3 +538,105 @@ def test_initial_phase_is_ill_conditioned():
     # iteration 0 costs agree; the phase cost after one step does not
     assert abs(c_pert[0, 2] - c_ref[0, 2]) < 1e-3 * c_ref[0, 2]
     assert abs(c_pert[1, 2] - c_ref[1, 2]) > 0.1 * c_ref[1, 2]
+
+
+# --------------------------------------------------------------------------- Sec. 4.1 evaluation
+def test_periodic_gaussian_kernel_and_circular_convolution():
+    """G of Eq. 20 (A19): unit sum, exp(-2/w^2) between neighbours; the direct circular sum (A20)
+    of a shifted delta is the shifted kernel, and it equals the convolution theorem's product."""
+    n, w = 12, 3.0
+    g = O.gaussian_kernel_periodic(n, w)
+    assert math.isclose(g.sum(), 1.0, rel_tol=1e-14)
+    assert math.isclose(g[0, 1] / g[0, 0], math.exp(-2.0 / w ** 2), rel_tol=1e-14)
+    assert math.isclose(g[1, 1] / g[0, 0], math.exp(-4.0 / w ** 2), rel_tol=1e-14)
+    assert np.allclose(g, g.T) and np.allclose(g[1:], g[1:][::-1])
+    delta = np.zeros((n, n))
+    delta[3, 5] = 1.0
+    assert np.allclose(O.circular_convolve(delta, g), np.roll(np.roll(g, 3, axis=0), 5, axis=1), atol=1e-16)
+    f = np.random.default_rng(81).standard_normal((n, n))
+    via_fft = np.real(np.fft.ifft2(np.fft.fft2(f) * np.fft.fft2(g)))
+    assert np.allclose(O.circular_convolve(f, g), via_fft, atol=1e-13)
+    h = np.random.default_rng(86).standard_normal((n, n))  # not symmetric: orientation matters
+    assert np.allclose(O.circular_convolve(f, h), np.real(np.fft.ifft2(np.fft.fft2(f) * np.fft.fft2(h))), atol=1e-12)
+
+
+def test_illumination_pattern_spans_one_minus_c_to_one():
+    zeta = np.random.default_rng(82).standard_normal((16, 16))
+    L = O.illumination_pattern(zeta, 0.3, 4.0)
+    assert math.isclose(L.min(), 0.7, rel_tol=1e-14) and math.isclose(L.max(), 1.0, rel_tol=1e-14)
+    assert np.all(O.illumination_pattern(np.full((8, 8), 2.5), 0.3, 4.0) == 0.7)
+
+
+def test_degrade_terms():
+    """Eqs. 2 / 20: with c = 0 the output minus the clean image is Omega + a xi exactly; the
+    salt & pepper rule maps u < d/2 to 0 and d/2 <= u < d to 1 and leaves the rest."""
+    g = np.random.default_rng(83)
+    I0 = g.uniform(0.1, 1.0, (3, 8, 8))
+    xi = g.standard_normal(I0.shape)
+    bg = np.array([0.01, 0.02, 0.03])
+    out = O.degrade(I0, background=bg, gauss_a=0.05, xi=xi)
+    assert np.allclose(out - I0, bg[:, None, None] + 0.05 * xi, atol=1e-15)
+    u = np.array([0.0, 0.049, 0.05, 0.0999, 0.1, 0.7]).reshape(1, 1, 6)
+    out = O.degrade(np.full((1, 1, 6), 0.4), snp_density=0.1, u_snp=u)
+    assert out.ravel().tolist() == [0.0, 0.0, 1.0, 1.0, 0.4, 0.4]
+    zeta = g.standard_normal(I0.shape)
+    out = O.degrade(I0, c=0.4, waist_px=3.0, zeta=zeta)
+    ratio = out / I0
+    assert np.allclose(ratio.min(axis=(1, 2)), 0.6) and np.allclose(ratio.max(axis=(1, 2)), 1.0)
+
+
+def test_noise_level_and_darkfield_selection():
+    """Eq. 21 on a hand example (10 % on the one dark image, bright images ignored) and the
+    dark-field rule |c_n| dk > NA / lambda with all LEDs of an image dark."""
+    I_sim = np.full((3, 4, 4), 2.0)
+    I_noi = I_sim.copy()
+    I_noi[1] += 0.2
+    I_noi[0] += 5.0
+    assert math.isclose(O.noise_level(I_sim, I_noi, [False, True, False]), 10.0, rel_tol=1e-14)
+    assert math.isclose(O.noise_level(I_sim, I_noi, [True, True, False]), (250.0 + 10.0) / 2, rel_tol=1e-14)
+    geo, _ = tiny_problem(n=16, u=2, grid=3, step=4, na_px=5.0)  # offsets 0, +-4 px; pupil radius 5 px
+    # the diagonal LEDs sit at 4 sqrt(2) = 5.66 px > 5: dark; the edge LEDs at 4 px: bright
+    assert O.darkfield_images(geo, 5.0 / 16, 1.0).tolist() == [True, False, True, False, False, False, True,
+                                                               False, True]
+    geo, _ = tiny_problem(n=16, u=4, grid=3, step=6, na_px=5.0)  # +-6 px: all but the centre are dark
+    dark = O.darkfield_images(geo, 5.0 / 16, 1.0)
+    assert dark.tolist() == [True] * 4 + [False] + [True] * 4
+    geo3 = O.make_geometry(16, 4, np.asarray(_grid_k(3, 6, 16)), na=5.0 / 16, wavelength_um=1.0, pixel_um=1.0,
+                           mux=3)
+    assert O.darkfield_images(geo3, 5.0 / 16, 1.0).tolist() == [True, False, True]
+
+
+def _grid_k(grid, step, n):
+    c = (np.arange(grid) - (grid - 1) // 2) * step
+    cy, cx = np.meshgrid(c, c, indexing="ij")
+    return np.stack([cx.ravel() / n, cy.ravel() / n], axis=1)
+
+
+def test_lsnr_is_the_maximum_over_b():
+    """Eq. 22: the closed-form b attains the maximum of the printed expression (checked on a
+    fine grid of b), a hand example, and invariance to a constant added to the estimate."""
+    g = np.random.default_rng(84)
+    truth = g.uniform(0.1, 1.0, 50)
+    rec = truth + 0.05 * g.standard_normal(50) + 0.3
+    val = O.lsnr(rec, truth)
+    bs = np.linspace(-1.0, 1.0, 200001)
+    d = truth[None, :] - rec[None, :] - bs[:, None]
+    brute = np.max(10 * np.log10(np.sum(truth ** 2) / np.sum(d ** 2, axis=1)))
+    assert val >= brute - 1e-9 and val - brute < 1e-6
+    assert math.isclose(O.lsnr(rec + 7.0, truth), val, rel_tol=1e-12)
+    # truth (1, 3), rec (0, 0): b = 2, residual (-1, 1), 10 log10(10 / 2)
+    assert math.isclose(O.lsnr([0.0, 0.0], [1.0, 3.0]), 10 * math.log10(5.0), rel_tol=1e-14)
+
+
+def test_object_quality_ignores_the_global_phase():
+    g = np.random.default_rng(85)
+    truth = g.uniform(0.2, 1.0, (8, 8)) * np.exp(1j * g.uniform(-1.0, 1.0, (8, 8)))
+    rec = truth + 0.01 * (g.standard_normal((8, 8)) + 1j * g.standard_normal((8, 8)))
+    a0, p0 = O.object_quality(rec, truth)
+    a1, p1 = O.object_quality(rec * np.exp(0.9j), truth)
+    assert math.isclose(a0, a1, rel_tol=1e-12) and math.isclose(p0, p1, rel_tol=1e-9)
+    assert 25.0 < a0 < 60.0 and 15.0 < p0 < 60.0
+    # phases spanning (-3, 3): a global phase left in place would wrap part of the map
+    truth = g.uniform(0.2, 1.0, (8, 8)) * np.exp(1j * g.uniform(-3.0, 3.0, (8, 8)))
+    rec = truth * np.exp(0.9j) * (1.0 + 1e-3 * g.standard_normal((8, 8)))
+    assert O.object_quality(rec, truth)[1] > 40.0
