@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the tensor-core precision leg")
     ap.add_argument("--no-fidelity", action="store_true", help="skip the fidelity-variant leg")
     ap.add_argument("--no-mux", action="store_true", help="skip the multiplexed-illumination leg")
+    ap.add_argument("--no-eval", action="store_true", help="skip the evaluation leg (Eqs. 20-22)")
     ap.add_argument("--serving-requests", type=int, default=120,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
@@ -329,6 +330,45 @@ def mux_leg(wid, w, obj_dev, torch, dev):
             "note": "traced steps; parity: tests/test_gpu_mux.py"}
 
 
+def eval_leg(wid, w, I_dev, obj_dev, torch, dev):
+    """Sec. 4.1 evaluation on the GPU for the benchmark workload: NL (Eq. 21) of its measurements
+    against the clean forward model at the true LED positions, and the amplitude / phase LSNR
+    (Eq. 22, global phase removed) of a 100-iteration reconstruction against the true object.
+    Also the time of one elf_degrade call (Eq. 20 uneven illumination c = 0.2 with w = 15 px,
+    Gaussian a = 1e-3, salt & pepper 0.05, background) over all 225 images, random fields given."""
+    from paper_2209_14671_gb300 import elfpie as E
+    stream = torch.cuda.current_stream(dev)
+    with E.Elf(w["n"], w["u"], w["k_xy_true"], w["na"], w["wavelength_um"], w["pixel_um"], stream=stream) as sim:
+        I_clean = torch.empty((w["K"], w["n"], w["n"]), dtype=torch.float32, device=dev)
+        sim.simulate(obj_dev, I_clean)
+        nl = sim.noise_level(I_clean, I_dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(20)
+        zeta = torch.randn(I_clean.shape, generator=g, device=dev)
+        xi = torch.randn(I_clean.shape, generator=g, device=dev)
+        u = torch.rand(I_clean.shape, generator=g, device=dev)
+        bg = 0.1 * torch.rand((w["K"],), generator=g, device=dev)
+        out = torch.empty_like(I_clean)
+        kw = dict(c=0.2, waist_px=15.0, zeta=zeta, background=bg, gauss_a=1e-3, xi=xi, snp_density=0.05, u_snp=u)
+        sim.degrade(I_clean, out, **kw)
+        t = []
+        for _ in range(5):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            sim.degrade(I_clean, out, **kw)  # synchronises
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            t.append(s0.elapsed_time(s1))
+    with E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"], stream=stream) as elf:
+        elf.set_measurements(I_dev)
+        elf.step(100)
+        la, lp = elf.object_quality(obj_dev)
+    return {"workload": w["name"], "nl_percent_darkfield": nl, "lsnr_amplitude_db_100_iters": la,
+            "lsnr_phase_db_100_iters": lp, "degrade_ms_225_images": float(np.median(t)),
+            "note": "parity: tests/test_gpu_eval.py; quality values have no counterpart in the paper "
+                    "(its images are not available)"}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -474,6 +514,11 @@ def run_ours(args):
     if not args.no_fidelity and world == 1:
         fidelity = fidelity_leg(w, I_dev, torch, dev)
 
+    evaluation = None
+    if not args.no_eval and world == 1:
+        obj = torch.from_numpy(IN.object_field(wid, w).astype(np.complex64)).to(dev)
+        evaluation = eval_leg(wid, w, I_dev, obj, torch, dev)
+
     mux = None
     if not args.no_mux and world == 1:
         obj = torch.from_numpy(IN.object_field(wid, w).astype(np.complex64)).to(dev)
@@ -516,6 +561,7 @@ def run_ours(args):
             "precision": precision,
             "fidelity_variants": fidelity,
             "multiplexed": mux,
+            "evaluation": evaluation,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

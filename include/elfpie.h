@@ -193,6 +193,42 @@ int elf_graph_kernel_count(elf_handle h);
  * pooled handles are freed, least recently used first, when a new shape needs
  * room.  A request's result is bitwise the same as a lone run of the same job. */
 typedef struct elf_server_s* elf_server;
+/* ---- evaluation of Sec. 4.1 (Eqs. 20-22); device pointers, the call synchronises ---- */
+
+/* Degradation parameters of Eqs. 2 and 20. */
+typedef struct {
+  double illum_c;      /* c of Eq. 20, in [0, 1]: the illumination factor spans [1 - c, 1]; 0 = none */
+  double waist_px;     /* 1/e^2 half-waist w of the Gaussian G of Eq. 20, low-res pixels (15 in Sec. 4.1) */
+  double gauss_a;      /* a of Eq. 20, Gaussian form: I += a * xi; 0 = none */
+  double snp_density;  /* a of Eq. 20, salt & pepper form, in [0, 1]: u < a/2 -> 0, a/2 <= u < a -> 1 */
+} elf_degrade_params;
+
+/* Eqs. 2 and 20 on the handle's image grid with caller-drawn random fields, per image j:
+ *   I_out = ((1 - c) + c * N(G (x) zeta_j)) * I_clean + background[j] + a * xi, then salt & pepper,
+ * where G (x) is the circular convolution with exp(-2 r^2 / w^2) normalised to unit sum and N the
+ * min-max normalisation to [0, 1] of each image (N = 0 for a flat field).  I_clean, zeta, xi,
+ * u_snp, I_out: [K/M][n][n] float on the device (I_out may not alias the inputs); background:
+ * [K/M] float on the device or NULL; a field may be NULL when its parameter is 0.
+ * Errors: ELF_EINVAL for missing fields or parameters out of range; n <= 1024. */
+int elf_degrade(elf_handle h, const float* I_clean, const float* zeta, const float* background,
+                const float* xi, const float* u_snp, const elf_degrade_params* prm, float* I_out);
+
+/* NL of Eq. 21 in percent: the mean over the handle's dark-field images (every LED of the image
+ * with |k| > NA / lambda) of ||I_sim - I_noised||_1 / ||I_sim||_1; 0 when there are none.
+ * I_sim, I_noised: [K/M][n][n] float on the device.  Writes *nl on the host. */
+int elf_noise_level(elf_handle h, const float* I_sim, const float* I_noised, double* nl);
+
+/* LSNR of Eq. 22 in dB: max over b of 10 log10(||truth||^2 / ||truth - (rec + b)||^2), attained
+ * at b = mean(truth - rec); sums in FP64.  rec, truth: count floats on the device; cuda_stream
+ * may be NULL.  Writes *out on the host. */
+int elf_lsnr(const float* rec, const float* truth, long long count, void* cuda_stream, double* out);
+
+/* LSNR (Eq. 22) of the amplitude and of the phase (atan2) of the handle's current object against
+ * the true object obj_true [N][N][2] float on the device, after multiplying the reconstruction
+ * by the least-squares global phase e^{i phi0}, phi0 = arg sum conj(O) O_true (the global phase
+ * is not observable from intensities).  Writes out2[0] (amplitude), out2[1] (phase) on the host. */
+int elf_object_quality(elf_handle h, const float* obj_true, double* out2);
+
 /* budget_bytes: device memory the server may hold; max_active: concurrent jobs. */
 int elf_server_create(size_t budget_bytes, int max_active, elf_server* out);
 /* Queues a request.  I [K][n][n] float (host; pinned memory makes the upload

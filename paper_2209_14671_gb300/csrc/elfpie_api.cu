@@ -53,6 +53,7 @@ struct elf_handle_s {
   int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;
   int mux = 1, n_img = 0;  // LEDs per measured image (Eq. 1) and the number of images K / mux
   double dk = 0.0;
+  double pupil_cut = 0.0;  // NA / lambda, the pupil radius in cycles/um
   elf_options opt{};
   cudaStream_t user = nullptr, cap = nullptr, aux = nullptr, paux = nullptr;  // paux: pupil chain
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr, ev_pp = nullptr,
@@ -513,7 +514,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
     }
   }
   // pupil support (reading A4), rows are contiguous runs of a disc
-  const double cut = (p->na / p->wavelength_um) * (p->na / p->wavelength_um);
+  h->pupil_cut = p->na / p->wavelength_um;
+  const double cut = h->pupil_cut * h->pupil_cut;
   std::vector<int> xs(n, 0), cnt(n, 0), off(n, 0), sidx_map(n * n, -1), supy, supx;
   int S = 0, Blo = -1, Bhi = -1;
   for (int jy = 0; jy < n; ++jy) {
@@ -737,6 +739,22 @@ int handle_sizes(elf_handle h, int* n, int* N, int* K) {
   return ELF_OK;
 }
 int handle_set_error(int code, const char* msg) { return set_error(code, msg); }
+int handle_image_info(elf_handle h, int* n, int* N, int* n_img) {
+  *n = h->n;
+  *N = h->N;
+  *n_img = h->n_img;
+  return ELF_OK;
+}
+// Dark-field images (Eq. 21): every LED of the image has |c_n| dk > NA / lambda.
+int handle_darkfield(elf_handle h, std::vector<unsigned char>& dark) {
+  dark.assign(h->n_img, 1);
+  const int off = h->N / 2 - h->n / 2;
+  for (int k = 0; k < h->K; ++k) {
+    const double cy = h->origin_h[k].x - off, cx = h->origin_h[k].y - off;
+    if (std::sqrt(cy * cy + cx * cx) * h->dk <= h->pupil_cut) dark[k / h->mux] = 0;
+  }
+  return ELF_OK;
+}
 
 }  // namespace elf
 

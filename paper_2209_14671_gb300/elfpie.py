@@ -35,6 +35,10 @@ class ElfOptions(ctypes.Structure):
                 ("tau_fid", c_double), ("tau_h", c_double), ("tile_dft", c_int), ("g_exponent", c_double)]
 
 
+class ElfDegradeParams(ctypes.Structure):
+    _fields_ = [("illum_c", c_double), ("waist_px", c_double), ("gauss_a", c_double), ("snp_density", c_double)]
+
+
 class ElfState(ctypes.Structure):
     _fields_ = [("psi", P_float), ("mu_psi", P_float), ("v_psi", P_float), ("delta_psi", P_float),
                 ("pupil", P_float), ("mu_pupil", P_float), ("v_pupil", P_float), ("delta_pupil", P_float),
@@ -70,6 +74,11 @@ SIGNATURES = {
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "elf_server_destroy": (None, [c_void_p]),
     "elf_estimate_weights_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "elf_degrade": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                            ctypes.POINTER(ElfDegradeParams), c_void_p]),
+    "elf_noise_level": (c_int, [c_void_p, c_void_p, c_void_p, P_double]),
+    "elf_lsnr": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p, P_double]),
+    "elf_object_quality": (c_int, [c_void_p, c_void_p, P_double]),
     "elf_destroy": (None, [c_void_p]),
     "elf_strerror": (ctypes.c_char_p, [c_int]),
     "elf_last_error": (ctypes.c_char_p, []),
@@ -122,6 +131,26 @@ def _ptr(x):
             raise ValueError("tensor must be contiguous")
         return x.data_ptr(), int(x.is_cuda)
     raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _dev_ptr(x) -> int:
+    """Device address of a contiguous CUDA tensor (0 for None); the evaluation calls take device memory."""
+    if x is None:
+        return 0
+    p, dev = _ptr(x)
+    if not dev:
+        raise ValueError("the evaluation calls take CUDA tensors")
+    return p
+
+
+def lsnr(rec, truth, stream=None) -> float:
+    """LSNR of Eq. 22 (dB) of two contiguous float32 CUDA tensors of equal size."""
+    if rec.numel() != truth.numel():
+        raise ValueError("rec and truth differ in size")
+    v = c_double()
+    _check(load().elf_lsnr(c_void_p(_dev_ptr(rec)), c_void_p(_dev_ptr(truth)), int(rec.numel()),
+                           c_void_p(_stream_handle(stream)), ctypes.byref(v)), "elf_lsnr")
+    return v.value
 
 
 def default_options(**overrides) -> ElfOptions:
@@ -282,6 +311,30 @@ class Elf:
 
     def kernels_per_step(self) -> int:
         return _check(load().elf_graph_kernel_count(self._h), "elf_graph_kernel_count")
+
+    # ------------------------------------------------------------ evaluation (Sec. 4.1)
+    def degrade(self, I_clean, out, c=0.0, waist_px=15.0, zeta=None, background=None, gauss_a=0.0, xi=None,
+                snp_density=0.0, u_snp=None):
+        """Eqs. 2 / 20 on device tensors [K/M, n, n] (background [K/M]) into ``out``."""
+        prm = ElfDegradeParams(float(c), float(waist_px), float(gauss_a), float(snp_density))
+        ptrs = [_dev_ptr(x) for x in (I_clean, zeta, background, xi, u_snp, out)]
+        _check(load().elf_degrade(self._h, *[c_void_p(p) for p in ptrs[:5]], ctypes.byref(prm), c_void_p(ptrs[5])),
+               "elf_degrade")
+        return out
+
+    def noise_level(self, I_sim, I_noised) -> float:
+        """NL of Eq. 21 (percent) of two device tensors [K/M, n, n] over the dark-field images."""
+        v = c_double()
+        _check(load().elf_noise_level(self._h, c_void_p(_dev_ptr(I_sim)), c_void_p(_dev_ptr(I_noised)),
+                                      ctypes.byref(v)), "elf_noise_level")
+        return v.value
+
+    def object_quality(self, obj_true):
+        """(amplitude LSNR, phase LSNR) of Eq. 22 of the current object against a device complex64
+        tensor [N, N], after the least-squares global phase."""
+        out = (c_double * 2)()
+        _check(load().elf_object_quality(self._h, c_void_p(_dev_ptr(obj_true)), out), "elf_object_quality")
+        return out[0], out[1]
 
     def simulate(self, obj, out=None):
         """Predicted intensities of Eq. 1 [K/M, n, n] float32 of the spatial object ``obj``
