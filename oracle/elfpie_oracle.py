@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` an
 
 Everything is complex128 / float64 NumPy, one operation per line, in the order of
 Algorithm 1 (Sec. 3.4).  The paper leaves several points silent or garbled; the
-readings taken here are labelled A1..A16 and listed with their reasons in the
+readings taken here are labelled A1..A20 and listed with their reasons in the
 design notes of the repository.  In short:
 
 * A1  transforms: Psi = fftshift(DFT_N(O)), O = IDFT_N(ifftshift(Psi)) (IDFT
@@ -15,7 +15,8 @@ design notes of the repository.  In short:
 * A5  nabla = forward differences with a Neumann (zero) last row/column.
 * A6  H = (Dxx, Dyy, sqrt2 Dxy) on the valid interior [1, N-2]^2.
 * A7  the L1 "gradient 0 at the origin" rule (Sec. 3.3) is a Huber smoothing:
-      phi(x) = |x| for |x| >= tau, |x|^2/(2 tau) + tau/2 below.
+      phi(x) = |x| for |x| >= tau, |x|^2/(2 tau) + tau/2 below; tau = 0 is the
+      paper literally, with omega = 0 where the feature is exactly 0.
 * A8  Eq. 11's residual is model minus measured in the intensity domain.
 * A9  initial state: Psi0 from the centre-LED image, mu = v = 0, delta = s0^2.
 * A10 alpha (Eq. 16): 'valid' 3x3 correlation, mean over the (n-2)^2 interior.
@@ -23,6 +24,11 @@ design notes of the repository.  In short:
 * A12 phase = atan2 without unwrapping.  A13 eta_H = 1e-12.  A14 eta_opt = 1e-8.
 * A15 pupil: P~ = G3 (x) P, P_new = mask o (P~ - Delta_P), gradient at P^t.
 * A16 s0_P = 1e-2.
+* A17 gamma / log fidelity (Sec. 6.3): g(x) = x^gamma or ln(x + 1) replaces
+      the identity (Eq. 5) or sqrt (Eq. 4) map of Eq. 3; measured intensities
+      are clamped at 0 before the map, and the slope g'(|o|^2) of the power map
+      takes |o| floored at eta_H, so gamma = 1/2 is exactly the amplitude form.
+      Eqs. 16-17 take g(max(I, 0)) for these maps.
 * A18 multiplexing (Eq. 1 with M > 1): LEDs in the caller's order, image j is
       lit by LEDs jM .. jM+M-1 (K a multiple of M); the residual of image j
       uses sum_m |o_{j,m}|^2; Psi0 comes from the image holding the centre LED.
@@ -30,11 +36,6 @@ design notes of the repository.  In short:
       1/e^2 radius; the blurred field min-max normalised to [0, 1] per image so
       that c sets the illumination range [1 - c, 1].
 * A20 that convolution is circular on the n x n image grid.
-* A17 gamma / log fidelity (Sec. 6.3): g(x) = x^gamma or ln(x + 1) replaces
-      the identity (Eq. 5) or sqrt (Eq. 4) map of Eq. 3; measured intensities
-      are clamped at 0 before the map, and the slope g'(|o|^2) of the power map
-      takes |o| floored at eta_H, so gamma = 1/2 is exactly the amplitude form.
-      Eqs. 16-17 take g(max(I, 0)) for these maps.
 
 Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
 (brute-force DFT, Parseval, adjoint identities, finite differences, affine null
@@ -215,19 +216,28 @@ def huber(comps, tau, iso):
     iso=1: phi = ||x||_2 if ||x|| >= tau else ||x||^2/(2 tau) + tau/2,
            omega = x / max(||x||, tau).
     iso=0: the same rule on each component separately (omega_i = x_i/max(|x_i|,tau)).
+    With tau = 0 (the paper literally) omega is 0 where the norm is 0: the L1 gradient
+    at the origin is taken as zero (Sec. 3.3).
     Returns (cost array, list of omega arrays).
     """
+    def ratio(c, den):
+        return np.divide(c, den, out=np.zeros_like(c), where=den > 0)
+
+    def smooth(a):
+        if tau <= 0:
+            return a
+        return np.where(a >= tau, a, a * a / (2.0 * tau) + tau / 2.0)
+
     if iso:
         norm = np.sqrt(sum(c * c for c in comps))
-        cost = np.where(norm >= tau, norm, norm * norm / (2.0 * tau) + tau / 2.0)
         den = np.maximum(norm, tau)
-        return cost, [c / den for c in comps]
+        return smooth(norm), [ratio(c, den) for c in comps]
     cost = np.zeros_like(comps[0])
     omegas = []
     for c in comps:
         a = np.abs(c)
-        cost = cost + np.where(a >= tau, a, a * a / (2.0 * tau) + tau / 2.0)
-        omegas.append(c / np.maximum(a, tau))
+        cost = cost + smooth(a)
+        omegas.append(ratio(c, np.maximum(a, tau)))
     return cost, omegas
 
 

@@ -62,7 +62,7 @@ struct elf_handle_s {
   bool tracing = false;
   int graph_kernels = 0;
   cudaEvent_t ev_stage[2 * ELF_NSTAGES] = {};
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {};  // iteration from psi_buf[p] into psi_buf[p ^ 1]
   std::vector<int2> origin_h;
   std::vector<int> sidx_h;  // linear support indices in compact order
   float gw0 = 0.f, gw1 = 0.f;
@@ -80,6 +80,11 @@ struct elf_handle_s {
   float* mux_r = nullptr;
   float* mux_f = nullptr;
   double* mux_cost = nullptr;
+  // Psi is double-buffered: an iteration reads psi_buf[cur] and its gather writes Psi^(t+1) into the
+  // other buffer, so that the Eq. 18 partials (which read Psi^t) need not finish before the gather;
+  // psi always points at the current buffer
+  float2* psi_buf[2] = {};
+  int cur = 0;
   float2 *psi = nullptr, *mu_psi = nullptr;
   float *v_psi = nullptr, *delta_psi = nullptr;
   float2 *pupil = nullptr, *pupil_next = nullptr, *mu_p = nullptr;
@@ -152,7 +157,9 @@ int mark(elf_handle h, cudaStream_t s, int stage, int end) {
   } while (0)
 
 // One outer iteration of Algorithm 1 (mode 0) or a gradient evaluation (mode 1).
-int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil) {
+// In mode 0 the gather writes Psi^(t+1) into psi_out (not psi, which the pupil chain still reads).
+int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil,
+                      float2* psi_out) {
   const bool pupil_path = (mode == 1) || h->opt.learn_pupil;
   const size_t A = (size_t)h->N * h->N;
   ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
@@ -305,8 +312,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.eta = (float)h->opt.eta_opt;
   pa.mode = mode;
   // the pupil chain (Eq. 18 partials, then the Eq. 19 update of P into pupil_next) on its own
-  // stream; the gather must wait for the partials, which read Psi before the gather updates it,
-  // but not for the pupil update, which overlaps the gather
+  // stream, beside the gather: the partials read Psi^t, which the gather leaves in place (it
+  // writes Psi^(t+1) into the other buffer)
   if (pupil_path) {
     ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_tile, 0));
     ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 0);
@@ -317,7 +324,6 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ELF_CK(launch_pupil_update(pa, h->paux));
     ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 1);
     ELF_CK(cudaEventRecord(h->ev_pu, h->paux));
-    ELF_CK(cudaStreamWaitEvent(s0, h->ev_pp, 0));
   }
 
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_join, 0));
@@ -331,7 +337,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.tile_ptr = h->tile_ptr;
   ga.tile_led = h->tile_led;
   ga.gH = h->q;
-  ga.psi = h->psi;
+  ga.psi = psi;
+  ga.psi_out = psi_out;
   ga.mu = h->mu_psi;
   ga.v = h->v_psi;
   ga.delta = h->delta_psi;
@@ -351,7 +358,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_CK(launch_gather(ga, s0));
   ELF_MARK(s0, ELF_STAGE_GATHER, 1);
   if (pupil_path) {
-    // P^t is read by the gather: P^(t+1) replaces it only after both
+    // P^t is read by the gather and the partials: P^(t+1) replaces it only after the gather and
+    // the whole pupil chain
     ELF_CK(cudaStreamWaitEvent(s0, h->ev_pu, 0));
     if (mode == 0)
       ELF_CK(cudaMemcpyAsync(h->pupil, h->pupil_next, (size_t)h->n * h->n * sizeof(float2),
@@ -365,34 +373,51 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
 }
 
 int build_graph(elf_handle h) {
-  if (h->graph) return ELF_OK;
-  cudaGraph_t g = nullptr;
-  ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_iteration(h, 0, h->cap, h->psi, h->pupil);
-  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-  if (rc != ELF_OK) {
-    if (g) cudaGraphDestroy(g);
-    return rc;
-  }
-  if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  size_t nn = 0;
-  h->graph_kernels = 0;
-  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
-      for (size_t i = 0; i < nn; ++i) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
-      }
-  }
-  // per-node priorities: the Hessian branch was captured from the high-priority stream
-  e = cudaGraphInstantiateWithFlags(&h->graph, g, cudaGraphInstantiateFlagUseNodePriority);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    h->graph = nullptr;
-    return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  if (h->graph[0] && h->graph[1]) return ELF_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (h->graph[p]) continue;
+    cudaGraph_t g = nullptr;
+    ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(h, 0, h->cap, h->psi_buf[p], h->pupil, h->psi_buf[p ^ 1]);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (rc != ELF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    size_t nn = 0;
+    h->graph_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
+        }
+    }
+    // per-node priorities: the Hessian branch was captured from the high-priority stream
+    e = cudaGraphInstantiateWithFlags(&h->graph[p], g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph[p] = nullptr;
+      return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
   }
   return ELF_OK;
+}
+
+void destroy_graphs(elf_handle h) {
+  for (cudaGraphExec_t& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Makes psi_buf[0] the current spectrum buffer (before writing a new state into it).
+void reset_current(elf_handle h) {
+  h->cur = 0;
+  h->psi = h->psi_buf[0];
 }
 
 // Powers gamma^(t+1) and bias corrections 1/(1 - gamma^(t+1)) of Eq. 19 for the
@@ -447,7 +472,7 @@ int elf_default_options(elf_options* o) {
 
 void elf_destroy(elf_handle h) {
   if (!h) return;
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  destroy_graphs(h);
   for (void* p : h->allocs) cudaFree(p);
   for (cudaEvent_t ev : h->ev_stage)
     if (ev) cudaEventDestroy(ev);
@@ -612,7 +637,9 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
     if ((rc = dalloc(h, &h->mux_f, nI))) return rc;
     if ((rc = dalloc(h, &h->mux_cost, (size_t)h->n_img * mux_blocks_per_image(n)))) return rc;
   }
-  if ((rc = dalloc(h, &h->psi, A))) return rc;
+  if ((rc = dalloc(h, &h->psi_buf[0], A))) return rc;
+  if ((rc = dalloc(h, &h->psi_buf[1], A))) return rc;
+  reset_current(h);
   if ((rc = dalloc(h, &h->mu_psi, A))) return rc;
   if ((rc = dalloc(h, &h->v_psi, A))) return rc;
   if ((rc = dalloc(h, &h->delta_psi, A))) return rc;
@@ -700,6 +727,7 @@ int init_state_async(elf_handle h) {
   // Psi0 from the image that holds the centre LED (its own image when mux = 1)
   ELF_CK(launch_init_small(h->I + (size_t)(h->centre / h->mux) * B, h->small, h->n, s));
   ELF_CK(launch_fft2(h->small, h->n, false, h->tw_n, s));
+  reset_current(h);  // the initial Psi goes into the first buffer
   ELF_CK(launch_embed(h->small, h->psi, h->n, h->N, h->origin_h[h->centre].x, h->origin_h[h->centre].y,
                       (float)(h->u * h->u), s));
   ELF_CK(launch_fill_f2(h->mu_psi, A, make_float2(0.f, 0.f), s));
@@ -786,7 +814,11 @@ int elf_step(elf_handle h, int n_iter) {
   if (!h->have_meas) return set_error(ELF_ESTATE, "elf_step before elf_set_measurements");
   if (n_iter < 0) return set_error(ELF_EINVAL, "negative n_iter");
   if (int rc = build_graph(h)) return rc;
-  for (int i = 0; i < n_iter; ++i) ELF_CK(cudaGraphLaunch(h->graph, h->user));
+  for (int i = 0; i < n_iter; ++i) {
+    ELF_CK(cudaGraphLaunch(h->graph[h->cur], h->user));
+    h->cur ^= 1;  // the iteration's Psi^(t+1) is in the other buffer
+    h->psi = h->psi_buf[h->cur];
+  }
   return ELF_OK;
 }
 
@@ -905,7 +937,7 @@ int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* co
   cudaStream_t s = h->user;
   ELF_CK(cudaMemcpyAsync(h->psi_eval, psi, A * 8, cudaMemcpyDefault, s));
   ELF_CK(cudaMemcpyAsync(h->pupil_eval, pupil, B * 8, cudaMemcpyDefault, s));
-  if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval)) return rc;
+  if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval, nullptr)) return rc;
   if (g_psi) ELF_CK(cudaMemcpyAsync(g_psi, h->g_psi, A * 8, cudaMemcpyDefault, s));
   if (g_pupil) ELF_CK(cudaMemcpyAsync(g_pupil, h->g_p, B * 8, cudaMemcpyDefault, s));
   double c[3];
@@ -996,10 +1028,9 @@ int elf_get_weights(elf_handle h, double* alpha, double* beta) {
 int elf_set_tracing(elf_handle h, int enable) {
   if (int rc = check(h)) return rc;
   const bool en = enable != 0;
-  if (en != h->tracing && h->graph) {
+  if (en != h->tracing && (h->graph[0] || h->graph[1])) {
     ELF_CK(cudaStreamSynchronize(h->user));
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
+    destroy_graphs(h);
   }
   h->tracing = en;
   return ELF_OK;

@@ -114,7 +114,9 @@ struct GatherArgs {
   const int* tile_ptr;    // tiles + 1
   const int* tile_led;    // LED lists per spectrum tile, ascending
   const float2* gH;       // N x N Hessian gradient (may be null)
-  float2* psi; float2* mu; float* v; float* delta;   // state (update mode)
+  const float2* psi;      // Psi^t
+  float2* psi_out;        // Psi^(t+1) (update mode; another buffer than psi)
+  float2* mu; float* v; float* delta;   // state (update mode, in place)
   float2* g_out;          // gradient output (gradient mode)
   const float* bc;        // Eq. 19 bias corrections 1/(1-g1^t), 1/(1-g2^t) of this iteration
   int N, n, S, K, tiles_x, max_list;

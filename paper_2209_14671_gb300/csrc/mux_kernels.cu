@@ -61,8 +61,8 @@ __device__ __forceinline__ Omega omega_at(float dx, float dy, float tau, int iso
     o.phi = (ss >= tau * tau) ? ss * inv : ss * hit + 0.5f * tau;
   } else {
     const float ax = fabsf(dx), ay = fabsf(dy);
-    o.wx = dx / fmaxf(ax, tau);
-    o.wy = dy / fmaxf(ay, tau);
+    o.wx = dx / fmaxf(ax, fmaxf(tau, 1e-18f));  // 0 at the origin when tau = 0
+    o.wy = dy / fmaxf(ay, fmaxf(tau, 1e-18f));
     o.phi = ((ax >= tau) ? ax : ax * ax * hit + 0.5f * tau) + ((ay >= tau) ? ay : ay * ay * hit + 0.5f * tau);
   }
   return o;

@@ -49,7 +49,7 @@ __device__ __forceinline__ float huber3(float& h0, float& h1, float& h2, float t
   for (int i = 0; i < 3; ++i) {
     const float a = fabsf(*hs[i]);
     c += (a >= tau) ? a : a * a / (2.f * tau) + 0.5f * tau;
-    *hs[i] /= fmaxf(a, tau);
+    *hs[i] /= fmaxf(a, fmaxf(tau, 1e-18f));  // 0 at the origin when tau = 0
   }
   return c;
 }
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
     return;
   }
   const float2 dlt = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
-  a.psi[k] = csub(ps, dlt);
+  a.psi_out[k] = csub(ps, dlt);
   a.mu[k] = mu;
   a.v[k] = v;
   a.delta[k] = dl;

@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(1024) tc_stencil_kernel(const TcArgs a) {
       phi = (ss >= tau * tau) ? ss * inv : ss * hit + 0.5f * tau;
     } else {
       const float ax = fabsf(dx), ay = fabsf(dy);
-      wx = dx / fmaxf(ax, tau);
-      wy = dy / fmaxf(ay, tau);
+      wx = dx / fmaxf(ax, fmaxf(tau, 1e-18f));  // 0 at the origin when tau = 0
+      wy = dy / fmaxf(ay, fmaxf(tau, 1e-18f));
       phi = ((ax >= tau) ? ax : ax * ax * hit + 0.5f * tau) + ((ay >= tau) ? ay : ay * ay * hit + 0.5f * tau);
     }
     WX[y * P + x] = wx;

@@ -309,3 +309,30 @@ def test_scaling_map_options_are_validated():
         with pytest.raises(E.ElfError) as ei:
             make_elf(c, **bad)
         assert ei.value.code == E.ELF_EINVAL
+
+
+@pytest.mark.parametrize("name", ["small32", "w0"])
+@pytest.mark.parametrize("iso", [1, 0])
+def test_plain_l1_tau_zero(name, iso):
+    """tau_fid = tau_h = 0: the paper's plain L1 terms with the gradient taken as 0 at the origin
+    (Sec. 3.3).  The normaliser is then discontinuous at 0, so features at the level of FP32
+    rounding turn into unit vectors whose direction rounding decides; the state after one
+    iteration is bounded at 1e-4 instead of 1e-5, and no value may be NaN (0/0 at exact zeros,
+    e.g. the Neumann last row and column, gives 0 on both sides)."""
+    variant = dict(tau_fid=0.0, tau_h=0.0, omega_iso=iso)
+    c = case(name)
+    st = developed_state(name, **variant)
+    I = c["I"].astype(np.float64)
+    opt = O.Options(**variant)
+    ref, costs_ref, _ = O.iteration(st, I, c["geo"], opt)
+    with make_elf(c, **variant) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        elf.step(1)
+        out = elf.get_state()
+        costs = elf.get_costs()[-1]
+    assert all(np.all(np.isfinite(out[k])) for k in ("psi", "pupil", "mu_psi", "v_psi", "delta_psi"))
+    e = dict(psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
+             cost=float(np.max(np.abs(costs - np.asarray(costs_ref)) / np.asarray(costs_ref))))
+    print(name, variant, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["cost"] < TOL_FWD

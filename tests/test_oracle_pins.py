@@ -640,3 +640,16 @@ def test_object_quality_ignores_the_global_phase():
     truth = g.uniform(0.2, 1.0, (8, 8)) * np.exp(1j * g.uniform(-3.0, 3.0, (8, 8)))
     rec = truth * np.exp(0.9j) * (1.0 + 1e-3 * g.standard_normal((8, 8)))
     assert O.object_quality(rec, truth)[1] > 40.0
+
+
+def test_normaliser_at_tau_zero_is_the_l1_subgradient_zero_at_the_origin():
+    """tau = 0 is the paper's plain L1 with its gradient taken as 0 at the origin (Sec. 3.3):
+    omega = x / |x| away from 0 and exactly 0 there, the cost |x|; no NaN anywhere."""
+    x = np.array([3.0, 0.0, -2.0, 0.0])
+    y = np.array([4.0, 0.0, 0.0, -1e-300])
+    cost, (wx, wy) = O.huber([x, y], 0.0, 1)
+    assert np.allclose(cost, np.hypot(x, y)) and np.all(np.isfinite(wx)) and np.all(np.isfinite(wy))
+    assert wx.tolist()[:3] == [0.6, 0.0, -1.0] and wy.tolist()[:3] == [0.8, 0.0, 0.0]
+    cost, (wx, wy) = O.huber([x, y], 0.0, 0)
+    assert np.allclose(cost, np.abs(x) + np.abs(y))
+    assert wx.tolist() == [1.0, 0.0, -1.0, 0.0] and wy.tolist() == [1.0, 0.0, 0.0, -1.0]
