@@ -50,7 +50,7 @@ int noalloc_set_error(int code, const char* msg) { return set_error(code, msg); 
 
 struct elf_handle_s {
   int n = 0, u = 0, N = 0, K = 0, S = 0, Blo = 0, nb = 0, rowsA = 0, cs = 1, Q = 1;
-  int hblocks = 0, tiles_x = 0, max_list = 0, centre = 0;
+  int hblocks = 0, tiles_x = 0, centre = 0;
   int mux = 1, n_img = 0;  // LEDs per measured image (Eq. 1) and the number of images K / mux
   double dk = 0.0;
   double pupil_cut = 0.0;  // NA / lambda, the pupil radius in cycles/um
@@ -70,7 +70,8 @@ struct elf_handle_s {
   int2* origin = nullptr;
   int *row_xs = nullptr, *row_cnt = nullptr, *row_off = nullptr;
   int *sup_y = nullptr, *sup_x = nullptr, *sidx_map = nullptr;
-  int *tile_ptr = nullptr, *tile_led = nullptr;
+  int* seg_ptr = nullptr;   // gather lists per (row, 32-pixel segment), CSR offsets
+  int4* seg_ent = nullptr;  // their entries
   float2 *tw_n = nullptr, *tw_N = nullptr;
   // data and state
   float* I = nullptr;
@@ -87,7 +88,10 @@ struct elf_handle_s {
   int cur = 0;
   float2 *psi = nullptr, *mu_psi = nullptr;
   float *v_psi = nullptr, *delta_psi = nullptr;
-  float2 *pupil = nullptr, *pupil_next = nullptr, *mu_p = nullptr;
+  // P is double-buffered like Psi (the Eq. 19 update writes P^(t+1) into the other buffer); with
+  // learn_pupil = 0 both iterations read pupil_buf[0].  pupil always points at the current buffer.
+  float2* pupil_buf[2] = {};
+  float2 *pupil = nullptr, *mu_p = nullptr;
   float *v_p = nullptr, *delta_p = nullptr;
   // scratch
   float2 *G = nullptr, *ot = nullptr, *q = nullptr, *small = nullptr, *part = nullptr;
@@ -157,9 +161,10 @@ int mark(elf_handle h, cudaStream_t s, int stage, int end) {
   } while (0)
 
 // One outer iteration of Algorithm 1 (mode 0) or a gradient evaluation (mode 1).
-// In mode 0 the gather writes Psi^(t+1) into psi_out (not psi, which the pupil chain still reads).
+// In mode 0 the gather writes Psi^(t+1) into psi_out (not psi, which the pupil chain still reads)
+// and the pupil update writes P^(t+1) into pupil_out (not pupil, which the gather still reads).
 int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil,
-                      float2* psi_out) {
+                      float2* psi_out, float2* pupil_out) {
   const bool pupil_path = (mode == 1) || h->opt.learn_pupil;
   const size_t A = (size_t)h->N * h->N;
   ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
@@ -293,7 +298,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.sidx_map = h->sidx_map;
   pa.part = h->part;
   pa.pupil = pupil;
-  pa.pupil_next = h->pupil_next;
+  pa.pupil_next = pupil_out;
   pa.mu = h->mu_p;
   pa.v = h->v_p;
   pa.delta = h->delta_p;
@@ -334,8 +339,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.row_xs = h->row_xs;
   ga.row_cnt = h->row_cnt;
   ga.row_off = h->row_off;
-  ga.tile_ptr = h->tile_ptr;
-  ga.tile_led = h->tile_led;
+  ga.seg_ptr = h->seg_ptr;
+  ga.seg_ent = h->seg_ent;
   ga.gH = h->q;
   ga.psi = psi;
   ga.psi_out = psi_out;
@@ -349,7 +354,6 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.S = h->S;
   ga.K = h->K;
   ga.tiles_x = h->tiles_x;
-  ga.max_list = h->max_list;
   ga.g1 = (float)h->opt.gamma1;
   ga.g2 = (float)h->opt.gamma2;
   ga.eta = (float)h->opt.eta_opt;
@@ -357,14 +361,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_MARK(s0, ELF_STAGE_GATHER, 0);
   ELF_CK(launch_gather(ga, s0));
   ELF_MARK(s0, ELF_STAGE_GATHER, 1);
-  if (pupil_path) {
-    // P^t is read by the gather and the partials: P^(t+1) replaces it only after the gather and
-    // the whole pupil chain
-    ELF_CK(cudaStreamWaitEvent(s0, h->ev_pu, 0));
-    if (mode == 0)
-      ELF_CK(cudaMemcpyAsync(h->pupil, h->pupil_next, (size_t)h->n * h->n * sizeof(float2),
-                             cudaMemcpyDeviceToDevice, s0));
-  }
+  if (pupil_path) ELF_CK(cudaStreamWaitEvent(s0, h->ev_pu, 0));  // the pupil chain joins the iteration
   // the cost reduction has read t before the iteration is closed
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_cost, 0));
   if (mode == 0) ELF_CK(launch_advance(h->t_dev, h->bc, h->gp, h->opt.gamma1, h->opt.gamma2, s0));
@@ -378,7 +375,9 @@ int build_graph(elf_handle h) {
     if (h->graph[p]) continue;
     cudaGraph_t g = nullptr;
     ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_iteration(h, 0, h->cap, h->psi_buf[p], h->pupil, h->psi_buf[p ^ 1]);
+    const bool lp = h->opt.learn_pupil != 0;
+    int rc = enqueue_iteration(h, 0, h->cap, h->psi_buf[p], h->pupil_buf[lp ? p : 0], h->psi_buf[p ^ 1],
+                               lp ? h->pupil_buf[p ^ 1] : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     if (rc != ELF_OK) {
       if (g) cudaGraphDestroy(g);
@@ -414,10 +413,11 @@ void destroy_graphs(elf_handle h) {
     }
 }
 
-// Makes psi_buf[0] the current spectrum buffer (before writing a new state into it).
+// Makes buffer 0 of Psi and P current (before writing a new state into them).
 void reset_current(elf_handle h) {
   h->cur = 0;
   h->psi = h->psi_buf[0];
+  h->pupil = h->pupil_buf[0];
 }
 
 // Powers gamma^(t+1) and bias corrections 1/(1 - gamma^(t+1)) of Eq. 19 for the
@@ -574,24 +574,29 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   h->rowsA = (h->nb + h->cs - 1) / h->cs;
   h->Q = pupil_chunks(K, S);
   h->hblocks = hess_blocks(N);
-  // per-tile LED lists for the gather (ascending LED order)
+  // gather lists (Eq. 9): for every spectrum row y and 32-pixel segment of it, the LEDs whose support
+  // chord on that row crosses the segment, in ascending LED order, each as {LED, offset of the row
+  // in the LED's compact G minus its first x, pupil index - x, first covered x | chord length << 16}
   h->tiles_x = N / kGatherTile;
-  std::vector<int> tptr(1, 0), tled;
-  for (int ty = 0; ty < h->tiles_x; ++ty)
-    for (int tx = 0; tx < h->tiles_x; ++tx) {
-      const int y0 = ty * kGatherTile, y1 = y0 + kGatherTile - 1, x0 = tx * kGatherTile, x1 = x0 + kGatherTile - 1;
-      int c = 0;
-      for (int k = 0; k < K; ++k) {
-        const int by0 = h->origin_h[k].x + Blo, by1 = h->origin_h[k].x + Bhi;
-        const int bx0 = h->origin_h[k].y + Blo, bx1 = h->origin_h[k].y + Bhi;  // the disc is symmetric
-        if (by1 < y0 || by0 > y1 || bx1 < x0 || bx0 > x1) continue;
-        tled.push_back(k);
-        ++c;
+  std::vector<int> sptr((size_t)N * h->tiles_x + 1, 0);
+  std::vector<int4> sent;
+  {
+    std::vector<std::vector<int4>> lists((size_t)N * h->tiles_x);
+    for (int k = 0; k < K; ++k) {
+      const int oy = h->origin_h[k].x, ox = h->origin_h[k].y;
+      for (int jy = 0; jy < n; ++jy) {
+        if (cnt[jy] == 0) continue;
+        const int y = oy + jy, lo = ox + xs[jy], hi = lo + cnt[jy];  // covered x in [lo, hi)
+        const int4 e = make_int4(k, off[jy] - lo, jy * n - ox, lo | (cnt[jy] << 16));
+        for (int tx = lo / kGatherTile; tx <= (hi - 1) / kGatherTile; ++tx) lists[(size_t)y * h->tiles_x + tx].push_back(e);
       }
-      if (c > h->max_list) h->max_list = c;
-      tptr.push_back((int)tled.size());
     }
-  if (h->max_list > 1024) return set_error(ELF_EINVAL, "more than 1024 LEDs overlap one 32x32 spectrum tile");
+    for (size_t i = 0; i < lists.size(); ++i) {
+      sptr[i + 1] = sptr[i] + (int)lists[i].size();
+      sent.insert(sent.end(), lists[i].begin(), lists[i].end());
+    }
+  }
+  if (sent.empty()) sent.push_back(make_int4(0, 0, 0, 0));
   // Gaussian 3x3, sigma = 1 px, normalised (note under Algorithm 1)
   const double e = std::exp(-0.5), tot = 1.0 + 2.0 * e;
   h->gw0 = (float)(1.0 / tot);
@@ -611,7 +616,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   ELF_CK(cudaEventCreateWithFlags(&h->ev_cost, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_pp, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_pu, cudaEventDisableTiming));
-  ELF_CK(cudaStreamCreateWithFlags(&h->paux, cudaStreamNonBlocking));
+  ELF_CK(cudaStreamCreateWithPriority(&h->paux, cudaStreamNonBlocking, prio_high));  // short pupil kernels first
   for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));
 
   // device memory
@@ -624,8 +629,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = upload(h, &h->sup_y, supy))) return rc;
   if ((rc = upload(h, &h->sup_x, supx))) return rc;
   if ((rc = upload(h, &h->sidx_map, sidx_map))) return rc;
-  if ((rc = upload(h, &h->tile_ptr, tptr))) return rc;
-  if ((rc = upload(h, &h->tile_led, tled))) return rc;
+  if ((rc = upload(h, &h->seg_ptr, sptr))) return rc;
+  if ((rc = upload(h, &h->seg_ent, sent))) return rc;
   if ((rc = upload(h, &h->tw_n, twiddles(n)))) return rc;
   if ((rc = upload(h, &h->tw_N, twiddles(N)))) return rc;
   const size_t nI = (size_t)h->n_img * B;
@@ -639,12 +644,12 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   }
   if ((rc = dalloc(h, &h->psi_buf[0], A))) return rc;
   if ((rc = dalloc(h, &h->psi_buf[1], A))) return rc;
-  reset_current(h);
   if ((rc = dalloc(h, &h->mu_psi, A))) return rc;
   if ((rc = dalloc(h, &h->v_psi, A))) return rc;
   if ((rc = dalloc(h, &h->delta_psi, A))) return rc;
-  if ((rc = dalloc(h, &h->pupil, B))) return rc;
-  if ((rc = dalloc(h, &h->pupil_next, B))) return rc;
+  if ((rc = dalloc(h, &h->pupil_buf[0], B))) return rc;
+  if ((rc = dalloc(h, &h->pupil_buf[1], B))) return rc;
+  reset_current(h);
   if ((rc = dalloc(h, &h->mu_p, B))) return rc;
   if ((rc = dalloc(h, &h->v_p, B))) return rc;
   if ((rc = dalloc(h, &h->delta_p, B))) return rc;
@@ -816,8 +821,9 @@ int elf_step(elf_handle h, int n_iter) {
   if (int rc = build_graph(h)) return rc;
   for (int i = 0; i < n_iter; ++i) {
     ELF_CK(cudaGraphLaunch(h->graph[h->cur], h->user));
-    h->cur ^= 1;  // the iteration's Psi^(t+1) is in the other buffer
+    h->cur ^= 1;  // the iteration's Psi^(t+1) and P^(t+1) are in the other buffers
     h->psi = h->psi_buf[h->cur];
+    if (h->opt.learn_pupil) h->pupil = h->pupil_buf[h->cur];
   }
   return ELF_OK;
 }
@@ -937,7 +943,7 @@ int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* co
   cudaStream_t s = h->user;
   ELF_CK(cudaMemcpyAsync(h->psi_eval, psi, A * 8, cudaMemcpyDefault, s));
   ELF_CK(cudaMemcpyAsync(h->pupil_eval, pupil, B * 8, cudaMemcpyDefault, s));
-  if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval, nullptr)) return rc;
+  if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval, nullptr, nullptr)) return rc;
   if (g_psi) ELF_CK(cudaMemcpyAsync(g_psi, h->g_psi, A * 8, cudaMemcpyDefault, s));
   if (g_pupil) ELF_CK(cudaMemcpyAsync(g_pupil, h->g_p, B * 8, cudaMemcpyDefault, s));
   double c[3];

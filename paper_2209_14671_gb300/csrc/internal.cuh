@@ -111,15 +111,16 @@ struct GatherArgs {
   const float2* pupil;    // n x n
   const int2* origin;     // K
   const int* row_xs; const int* row_cnt; const int* row_off;
-  const int* tile_ptr;    // tiles + 1
-  const int* tile_led;    // LED lists per spectrum tile, ascending
+  const int* seg_ptr;     // N * tiles_x + 1 offsets of the lists per (row, 32-pixel segment)
+  const int4* seg_ent;    // entries, ascending LED: {LED, compact G row offset - first x, pupil index - x,
+                          // first x | count << 16}
   const float2* gH;       // N x N Hessian gradient (may be null)
   const float2* psi;      // Psi^t
   float2* psi_out;        // Psi^(t+1) (update mode; another buffer than psi)
   float2* mu; float* v; float* delta;   // state (update mode, in place)
   float2* g_out;          // gradient output (gradient mode)
   const float* bc;        // Eq. 19 bias corrections 1/(1-g1^t), 1/(1-g2^t) of this iteration
-  int N, n, S, K, tiles_x, max_list;
+  int N, n, S, K, tiles_x;
   float g1, g2, eta;
   int mode;               // 0 = AdaBelief update, 1 = write g
 };

@@ -182,20 +182,14 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
   return d;
 }
 
-constexpr int kMaxTileList = 1024;
-
-// One thread per spectrum pixel; a block covers 32 x 8 pixels of one 32 x 32
-// gather tile, whose ascending LED list it stages in shared memory.
+// One thread per spectrum pixel; a block covers 32 x 8 pixels, each warp one 32-pixel segment of a
+// row, whose list holds exactly the LEDs with a support chord crossing the segment (ascending).
 __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
-  __shared__ int s_led[kMaxTileList];
-  __shared__ int2 s_org[kMaxTileList];
-  extern __shared__ int s_rows[];   // row_xs, row_cnt, row_off (n each)
-  const int tid = threadIdx.y * 32 + threadIdx.x;
   const int x = blockIdx.x * kGatherTile + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
-  const int tile = (blockIdx.y / (kGatherTile / 8)) * a.tiles_x + blockIdx.x;
-  const int l0 = a.tile_ptr[tile], cnt = a.tile_ptr[tile + 1] - l0;
   const size_t k = (size_t)y * a.N + x;
+  const int seg = y * a.tiles_x + blockIdx.x;
+  const int e0 = a.seg_ptr[seg], e1 = a.seg_ptr[seg + 1];
   // state loads first, so that they are in flight during the LED loop
   float2 g = a.gH ? a.gH[k] : make_float2(0.f, 0.f);
   float2 mu = make_float2(0.f, 0.f), ps = make_float2(0.f, 0.f);
@@ -206,41 +200,24 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
     dl = a.delta[k];
     ps = a.psi[k];
   }
-  if (cnt > 0) {
-    for (int i = tid; i < cnt; i += 256) {
-      const int led = a.tile_led[l0 + i];
-      s_led[i] = led;
-      s_org[i] = a.origin[led];
-    }
-    for (int i = tid; i < a.n; i += 256) {
-      s_rows[i] = a.row_xs[i];
-      s_rows[a.n + i] = a.row_cnt[i];
-      s_rows[2 * a.n + i] = a.row_off[i];
-    }
-  }
-  __syncthreads();
-  // covering LEDs in ascending list order; the loads of four list entries are issued before
-  // their products are added (same additions in the same order as one entry at a time)
+  // covering LEDs in ascending order; the loads of four entries are issued before their products
+  // are added (same additions in the same order as one entry at a time)
   float2 acc = make_float2(0.f, 0.f);
   constexpr int U = 4;
-  for (int i0 = 0; i0 < cnt; i0 += U) {
+  for (int i0 = e0; i0 < e1; i0 += U) {
     float2 p[U], gt[U];
     bool ok[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = i0 + u;
       ok[u] = false;
       p[u] = gt[u] = make_float2(0.f, 0.f);
-      if (i < cnt) {
-        const int2 o = s_org[i];
-        const int jy = y - o.x, jx = x - o.y;
-        if ((unsigned)jy < (unsigned)a.n) {
-          const int d = jx - s_rows[jy];
-          if ((unsigned)d < (unsigned)s_rows[a.n + jy]) {
-            ok[u] = true;
-            p[u] = a.pupil[jy * a.n + jx];
-            gt[u] = a.G[(size_t)s_led[i] * a.S + s_rows[2 * a.n + jy] + d];
-          }
+      if (i0 + u < e1) {
+        const int4 e = __ldg(&a.seg_ent[i0 + u]);  // the same entry for the whole warp
+        const int lo = e.w & 0xffff, cnt = e.w >> 16;
+        if ((unsigned)(x - lo) < (unsigned)cnt) {
+          ok[u] = true;
+          p[u] = a.pupil[e.z + x];
+          gt[u] = a.G[(size_t)e.x * a.S + e.y + x];
         }
       }
     }
@@ -261,9 +238,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
 }
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
-  if (a.max_list > kMaxTileList) return cudaErrorInvalidValue;
   dim3 grid(a.tiles_x, a.N / 8), block(32, 8);
-  gather_kernel<<<grid, block, 3 * a.n * sizeof(int), s>>>(a);
+  gather_kernel<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 
