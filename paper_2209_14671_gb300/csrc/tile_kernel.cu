@@ -151,8 +151,22 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const size_t meas_img = (size_t)(a.mode == 2 ? led / a.mux : led) * NL * NL;
   const bool has_meas = a.mode != 1;
 
-  // twiddles (group 0) and this CTA's columns of I_n (group 1, overlapping stages A and B)
-  // arrive by cp.async in 16-byte chunks
+  const int b0 = crank * a.rowsA;
+  const int nrows = max(0, min(a.nb - b0, a.rowsA));
+  // cp.async groups: 0 = the spectrum crop of this team's first band row (into its row buffer, at
+  // its natural column index), 1 = the twiddles, 2 = this CTA's columns of I_n (overlapping stages
+  // A and B).  The crop goes first so that its L2 latency overlaps the rest of the prologue.
+  const int2 org = a.origin[led];
+  if (team < nrows) {
+    const int y = a.Blo + b0 + team;
+    const unsigned ch = a.chord[y];
+    const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
+    const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
+    const unsigned rbase = (unsigned)__cvta_generic_to_shared(A1 + team * RP);
+    for (int x = xs + lane; x < xs + cnt; x += TL)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(rbase + 8u * x), "l"(prow + x) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   {
     const unsigned tbase = (unsigned)__cvta_generic_to_shared(tw);
     for (int i = tid; i < NL / 2; i += NT)
@@ -179,8 +193,6 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  const int b0 = crank * a.rowsA;
-  const int nrows = max(0, min(a.nb - b0, a.rowsA));
   // mbarriers of the two exchanges into this CTA: [0] the stage A rows of its owned and halo
   // columns (every band row, CW columns plus a halo column on each inner side), [1] its stage C
   // rows (all n columns of each of its band rows)
@@ -198,8 +210,6 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // overlaps the crop loads and the first transforms.
   cluster_arrive<CS>();
 
-  const int2 org = a.origin[led];
-
   // ---- A: inverse row transforms of this CTA's band rows, pushed into the column owners
   for (int base = 0; base < a.rowsA; base += NTEAM) {
     const int lb = base + team;
@@ -207,12 +217,21 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     float2* row = A1 + (act ? lb : 0) * RP;
     const int y = a.Blo + b0 + (act ? lb : 0);
     const int py = FftTeam<NL>::pidx(y);
-    // crop x pupil straight into the registers of the transform's first pass (x = lane + TL j);
-    // every load is issued before the first product
+    if (base == 0) {  // the crops and twiddles (cp.async groups 0, 1) have landed, visible CTA-wide
+      if (has_meas) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      __syncthreads();
+    }
+    // crop x pupil into the registers of the transform's first pass (x = lane + TL j): the first
+    // row's crop from the row buffer, later rows' straight from global memory
     constexpr int PL = FftTeam<NL>::P;
     float2 v[PL];
     if (act) {
-      const int xs = a.row_xs[y], cnt = a.row_cnt[y];
+      const unsigned ch = a.chord[y];
+      const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
       const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
       const float2* pp = a.pupil + (size_t)y * NL;
       float2 pv[PL];
@@ -221,18 +240,10 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         const int x = lane + TL * j;
         const bool in = (unsigned)(x - xs) < (unsigned)cnt;
         pv[j] = in ? pp[x] : make_float2(0.f, 0.f);
-        v[j] = in ? prow[x] : make_float2(0.f, 0.f);
+        v[j] = in ? (base == 0 ? row[x] : prow[x]) : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
-    }
-    if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
-      if (has_meas) {
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      }
-      __syncthreads();
     }
     team_fft_core<NL, true>(v, row, tw, lane, act);
     if (base == 0) cluster_wait<CS>();
@@ -481,8 +492,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     team_fft_core<NL, false>(v, row, tw, lane, act);
     if (act) {
       const int ky = a.Blo + b0 + lb;
-      const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
-      float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
+      const unsigned ch = a.chord[ky];
+      const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
+      float2* dst = a.G + (size_t)led * a.S + a.choff[ky];
 #pragma unroll
       for (int m = 0; m < PL / Q; ++m) {
 #pragma unroll
