@@ -65,8 +65,6 @@ struct elf_handle_s {
   cudaGraphExec_t graph[2] = {};  // iteration from psi_buf[p] into psi_buf[p ^ 1]
   std::vector<int2> origin_h;
   std::vector<int> sidx_h;  // linear support indices in compact order
-  std::vector<unsigned> chord_h;  // per pupil row: first support column | count << 16
-  std::vector<int> choff_h;       // per pupil row: compact index of its first support pixel
   float gw0 = 0.f, gw1 = 0.f;
   // device tables
   int2* origin = nullptr;
@@ -163,12 +161,6 @@ int mark(elf_handle h, cudaStream_t s, int stage, int end) {
   } while (0)
 
 // One outer iteration of Algorithm 1 (mode 0) or a gradient evaluation (mode 1).
-// The support chords of the pupil rows, passed to the tile kernel as parameters.
-void set_chords(elf_handle h, TileArgs& ta) {
-  std::memcpy(ta.chord, h->chord_h.data(), sizeof(ta.chord));
-  std::memcpy(ta.choff, h->choff_h.data(), sizeof(ta.choff));
-}
-
 // In mode 0 the gather writes Psi^(t+1) into psi_out (not psi, which the pupil chain still reads)
 // and the pupil update writes P^(t+1) into pupil_out (not pupil, which the gather still reads).
 int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil,
@@ -199,7 +191,6 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
 
   // tile path: Eqs. 1, 5 (4), 12, 11 (10) and F_B^H of Eq. 9
   TileArgs ta{};
-  set_chords(h, ta);
   ta.psi = psi;
   ta.pupil = pupil;
   ta.meas = h->opt.fidelity >= 1 ? h->Ig : h->I;
@@ -635,12 +626,6 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = upload(h, &h->row_xs, xs))) return rc;
   if ((rc = upload(h, &h->row_cnt, cnt))) return rc;
   if ((rc = upload(h, &h->row_off, off))) return rc;
-  h->chord_h.assign(kTileMaxN, 0u);
-  h->choff_h.assign(kTileMaxN, 0);
-  for (int jy = 0; jy < n; ++jy) {
-    h->chord_h[jy] = (unsigned)xs[jy] | ((unsigned)cnt[jy] << 16);
-    h->choff_h[jy] = off[jy];
-  }
   if ((rc = upload(h, &h->sup_y, supy))) return rc;
   if ((rc = upload(h, &h->sup_x, supx))) return rc;
   if ((rc = upload(h, &h->sidx_map, sidx_map))) return rc;
@@ -992,7 +977,6 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
     dst = staging;
   }
   TileArgs ta{};
-  set_chords(h, ta);
   ta.psi = h->psi_eval;
   ta.pupil = h->pupil_unit;
   ta.origin = h->origin;

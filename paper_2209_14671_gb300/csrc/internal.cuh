@@ -11,7 +11,6 @@ constexpr int kGatherTile = 32;   // spectrum tile side of the gather lists
 constexpr int kCostRing = 4096;   // iterations kept in the cost ring buffer
 
 // ---------------------------------------------------------------- tile kernel
-constexpr int kTileMaxN = 256;    // largest low-res side of the tile kernel
 // One cluster of CS CTAs per LED runs Eqs. 1, 5/4, 12, 11/10 and F_B^H of Eq. 9.
 struct TileArgs {
   const float2* psi;      // N x N centred spectrum
@@ -34,10 +33,6 @@ struct TileArgs {
   int mode;               // 0 = gradient, 1 = simulate |o|^2, 2 = gradient of multiplexed images:
                           // meas holds the per-image factor f (mux_kernels.cu), W = o f
   int mux;                // M: LEDs per image; LED k reads image k / M in mode 2
-  // support chords of the pupil rows as kernel parameters (read through the constant cache):
-  // chord[y] = first column | count << 16, choff[y] = compact index of its first pixel
-  unsigned chord[kTileMaxN];
-  int choff[kTileMaxN];
 };
 int tile_cluster_size(int n);
 int tile_warps(int n);                        // warps per CTA of the tile kernel

@@ -119,22 +119,6 @@ struct OmegaOut {
 // map of Sec. 6.3 (power or log, chosen at run time by a.fidelity = 2 or 3; meas holds g(max(I, 0))); ISO: 1 = isotropic
 // normaliser, 0 = anisotropic (Eq. 12).  Compile-time, so the per-pixel loops carry no untaken branch
 // work in the two forms of the paper's Eqs. 4-5.
-// Shared memory of the tile kernel: I tile and halo, twiddles, band rows, column buffer, Hx, two
-// mbarriers; the pupil rows of the first stage A round are staged too when they fit.
-__host__ __device__ constexpr int team_lanes(int n) {
-  int lg = 0;
-  while ((1 << lg) < n) ++lg;
-  return 1 << (lg / 2);
-}
-__host__ __device__ constexpr size_t tile_smem_base(int n, int cs, int rowsA) {
-  const size_t rp = (size_t)(n + n / team_lanes(n));  // padded FFT buffer length
-  return 4 * (size_t)n * (n / cs + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
-         4 * 2 * (size_t)n + 16;
-}
-__host__ __device__ constexpr bool tile_prow_fits(int n, int cs, int rowsA) {
-  return tile_smem_base(n, cs, rowsA) + 8 * (size_t)rowsA * n <= (size_t)227 * 1024;
-}
-
 template <int NL, int CS, int NT, int FID, int ISO>
 __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   constexpr int NW = NT / 32;
@@ -153,8 +137,6 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   float2* A1 = tw + NL;                                   // rowsA band rows of pitch RP
   float2* OC = A1 + a.rowsA * RP;                         // RP rows of PO: row pidx(y), column 1 + x - x0
   float* Hx = reinterpret_cast<float*>(OC + RP * PO);     // 2 x NL: r at x0+CW, omega_x at x0-1
-  // after the two mbarriers: rowsA x NL pupil values of the CTA's band rows (stage A's first round)
-  float2* Prow = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Hx + 2 * NL) + 16);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, wl = tid & 31;
@@ -169,36 +151,11 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const size_t meas_img = (size_t)(a.mode == 2 ? led / a.mux : led) * NL * NL;
   const bool has_meas = a.mode != 1;
 
-  const int b0 = crank * a.rowsA;
-  const int nrows = max(0, min(a.nb - b0, a.rowsA));
-  // cp.async groups: 0 = the spectrum crop and the pupil values of this team's first band row
-  // (into its row buffer and its Prow row, at their natural column index), 1 = the twiddles, 2 =
-  // this CTA's columns of I_n (overlapping stages A and B).  The crop goes first so that its L2
-  // latency overlaps the rest of the prologue, and the twiddles and I_n are issued by the warps
-  // that hold no stage A row (all warps when fewer than two are free).
-  const int2 org = a.origin[led];
-  const bool staged_p = tile_prow_fits(NL, CS, a.rowsA);  // pupil rows staged in shared memory
-  if (team < nrows) {
-    const int y = a.Blo + b0 + team;
-    const unsigned ch = a.chord[y];
-    const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
-    const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
-    const float2* pp = a.pupil + (size_t)y * NL;
-    const unsigned rbase = (unsigned)__cvta_generic_to_shared(A1 + team * RP);
-    const unsigned pbase = (unsigned)__cvta_generic_to_shared(Prow + team * NL);
-    for (int x = xs + lane; x < xs + cnt; x += TL) {
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(rbase + 8u * x), "l"(prow + x) : "memory");
-      if (staged_p)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(pbase + 8u * x), "l"(pp + x) : "memory");
-    }
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  int t0 = ((nrows * TL + 31) / 32) * 32;  // first thread of the warps without a stage A row
-  if (NT - t0 < 64) t0 = 0;
-  const int tl = tid - t0, nl = NT - t0;  // this thread's rank among the loaders (tl < 0: none)
+  // twiddles (group 0) and this CTA's columns of I_n (group 1, overlapping stages A and B)
+  // arrive by cp.async in 16-byte chunks
   {
     const unsigned tbase = (unsigned)__cvta_generic_to_shared(tw);
-    for (int i = tl; i >= 0 && i < NL / 2; i += nl)
+    for (int i = tid; i < NL / 2; i += NT)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tbase + 16u * i), "l"(a.tw + 2 * i)
                    : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -206,13 +163,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   if (has_meas) {
     constexpr int CH = CW / 4;  // 16-byte chunks per row
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(Itile);
-    for (int i = tl; i >= 0 && i < NL * CH; i += nl) {
+    for (int i = tid; i < NL * CH; i += NT) {
       const int y = i / CH, k = i - y * CH;
       const float* src = a.meas + meas_img + (size_t)y * NL + x0 + 4 * k;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 4u * (y * CW + 4 * k)), "l"(src)
                    : "memory");
     }
-    for (int i = tl; i >= 0 && i < (a.mode == 0 ? 2 * NL : 0); i += nl) {  // halo columns: mode 0 only
+    for (int i = tid; i < (a.mode == 0 ? 2 * NL : 0); i += NT) {  // halo columns: mode 0 only
       const int side = i / NL, y = i - side * NL;
       const int x = side ? x0 + CW : x0 - 1;
       if (x < 0 || x >= NL) continue;
@@ -222,13 +179,14 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
+  const int b0 = crank * a.rowsA;
+  const int nrows = max(0, min(a.nb - b0, a.rowsA));
   // mbarriers of the two exchanges into this CTA: [0] the stage A rows of its owned and halo
   // columns (every band row, CW columns plus a halo column on each inner side), [1] its stage C
   // rows (all n columns of each of its band rows)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Hx + 2 * NL);
-  // (initialised by the last warp, so that the cluster-scope fence delays no stage A row)
   if constexpr (CS > 1) {
-    if (tid == NT - 32) {
+    if (tid == 0) {
       const int cols = CW + (crank > 0 ? 1 : 0) + (crank < CS - 1 ? 1 : 0);
       mbar_init_expect(&mbar[0], (uint32_t)(a.nb * cols * 8));
       mbar_init_expect(&mbar[1], (uint32_t)(nrows * NL * 8));
@@ -240,6 +198,8 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // overlaps the crop loads and the first transforms.
   cluster_arrive<CS>();
 
+  const int2 org = a.origin[led];
+
   // ---- A: inverse row transforms of this CTA's band rows, pushed into the column owners
   for (int base = 0; base < a.rowsA; base += NTEAM) {
     const int lb = base + team;
@@ -247,21 +207,12 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     float2* row = A1 + (act ? lb : 0) * RP;
     const int y = a.Blo + b0 + (act ? lb : 0);
     const int py = FftTeam<NL>::pidx(y);
-    if (base == 0) {  // the crops and twiddles (cp.async groups 0, 1) have landed, visible CTA-wide
-      if (has_meas) {
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      }
-      __syncthreads();
-    }
-    // crop x pupil into the registers of the transform's first pass (x = lane + TL j): the first
-    // row's crop from the row buffer, later rows' straight from global memory
+    // crop x pupil straight into the registers of the transform's first pass (x = lane + TL j);
+    // every load is issued before the first product
     constexpr int PL = FftTeam<NL>::P;
     float2 v[PL];
     if (act) {
-      const unsigned ch = a.chord[y];
-      const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
+      const int xs = a.row_xs[y], cnt = a.row_cnt[y];
       const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
       const float2* pp = a.pupil + (size_t)y * NL;
       float2 pv[PL];
@@ -269,11 +220,19 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       for (int j = 0; j < PL; ++j) {
         const int x = lane + TL * j;
         const bool in = (unsigned)(x - xs) < (unsigned)cnt;
-        pv[j] = in ? ((base == 0 && staged_p) ? Prow[team * NL + x] : pp[x]) : make_float2(0.f, 0.f);
-        v[j] = in ? (base == 0 ? row[x] : prow[x]) : make_float2(0.f, 0.f);
+        pv[j] = in ? pp[x] : make_float2(0.f, 0.f);
+        v[j] = in ? prow[x] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
+    }
+    if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
+      if (has_meas) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+      __syncthreads();
     }
     team_fft_core<NL, true>(v, row, tw, lane, act);
     if (base == 0) cluster_wait<CS>();
@@ -522,9 +481,8 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
     team_fft_core<NL, false>(v, row, tw, lane, act);
     if (act) {
       const int ky = a.Blo + b0 + lb;
-      const unsigned ch = a.chord[ky];
-      const int xs = (int)(ch & 0xffffu), cnt = (int)(ch >> 16);
-      float2* dst = a.G + (size_t)led * a.S + a.choff[ky];
+      const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
+      float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
 #pragma unroll
       for (int m = 0; m < PL / Q; ++m) {
 #pragma unroll
@@ -556,7 +514,10 @@ static int tile_threads(int n) {
 }
 
 size_t tile_smem_bytes(int n, int cs, int rowsA) {
-  return tile_smem_base(n, cs, rowsA) + (tile_prow_fits(n, cs, rowsA) ? 8 * (size_t)rowsA * n : 0);
+  const size_t rp = fft_padded_length(n);
+  const size_t cw = n / cs;
+  return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
+         4 * 2 * (size_t)n + 16;  // ... + Hx + two mbarriers
 }
 
 int tile_warps(int n) { return tile_threads(n) / 32; }
