@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-fidelity", action="store_true", help="skip the fidelity-variant leg")
     ap.add_argument("--no-mux", action="store_true", help="skip the multiplexed-illumination leg")
     ap.add_argument("--no-eval", action="store_true", help="skip the evaluation leg (Eqs. 20-22)")
-    ap.add_argument("--serving-requests", type=int, default=120,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
 

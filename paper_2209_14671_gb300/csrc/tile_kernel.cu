@@ -441,11 +441,29 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   }
   __syncthreads();  // W is complete in every column before the column transforms read it
 
-  // forward column transforms of the owned columns, then push the band rows to their owners
+  // forward column transforms of the owned columns (only the support band rows of the output are
+  // written back: the other rows are never read), then push the band rows to their owners
   for (int base = 0; base < CW; base += NTEAM) {
     const int cw = base + team;
     const bool act = cw < CW;
-    team_fft<NL, false, PO>(OC + (act ? cw + 1 : 1), tw, lane, act);
+    float2* col = OC + (act ? cw + 1 : 1);
+    constexpr int PL = FftTeam<NL>::P, Q = FftTeam<NL>::Q;
+    float2 v[PL];
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < PL; ++j) v[j] = col[(lane + (Q + 1) * j) * PO];
+    }
+    team_fft_core<NL, false, PO>(v, col, tw, lane, act);
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < PL / Q; ++m) {
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int k = lane + Q * m + PL * k2;
+          if ((unsigned)(k - a.Blo) < (unsigned)a.nb) col[FftTeam<NL>::pidx(k) * PO] = v[m * Q + k2];
+        }
+      }
+    }
   }
   __syncthreads();
   for (int b = warp; b < a.nb; b += NW) {
