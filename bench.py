@@ -431,12 +431,13 @@ def run_ours(args):
     # stage breakdown (not timed for the metric): the same steps with CUDA events recorded
     # inside the graph around each stage, on the stream each stage runs on
     elf.set_tracing(True)
-    stage_ms = []
+    stage_ms, stage_spans = [], []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         elf.step(1)
         if i >= args.warmup:
             stage_ms.append(elf.stage_times())  # synchronises after the step
+            stage_spans.append(elf.stage_spans())
     elf.set_tracing(False)
     kernels_per_step = elf.kernels_per_step()
 
@@ -480,6 +481,8 @@ def run_ours(args):
         if tr.get("sources_sha256_16") == tile_sources_hash() and tr.get("workload") == w["name"]:
             traffic = tr.get("dram_bytes_per_launch")
     stage_mean = {k: float(np.mean([s[k] for s in stage_ms])) for k in stage_ms[0]}
+    span_median = {k: [round(float(np.median([s[k][e] for s in stage_spans])), 4) for e in (0, 1)]
+                   for k in stage_spans[0]}
     it_bytes = w["K"] * (4 * w["n"] ** 2 + 32 * S) + 72 * w["N"] ** 2
 
     # end to end through the public API with host buffers: one full reconstruction per step
@@ -554,6 +557,7 @@ def run_ours(args):
             "iteration_roofline": {"algorithmic_bytes": it_bytes, "achieved_gbs": it_bytes / (total_ms / args.steps / 1e3) / 1e9,
                                    "frac": it_bytes / (total_ms / args.steps / 1e3) / 1e9 / hbm},
             "stage_ms": stage_mean,
+            "stage_spans_ms": span_median,
             "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "e2e": e2e,

@@ -181,6 +181,10 @@ int elf_set_tracing(elf_handle h, int enable);
 /* Durations in ms of each stage of the most recent traced iteration, ms[ELF_NSTAGES]
  * (-1 for a stage that did not run).  Synchronises.  Returns the count written. */
 int elf_get_stage_times(elf_handle h, float* ms, int max_stages);
+/* Start and end of each stage of the most recent traced iteration in ms from the iteration's
+ * start, spans[2 * stage] and spans[2 * stage + 1] (-1 for a stage that did not run): which
+ * stream's chain ends the iteration.  Synchronises.  Returns the count of stages written. */
+int elf_get_stage_spans(elf_handle h, float* spans, int max_stages);
 /* Number of kernel launches in one iteration (kernel nodes of the iteration graph). */
 int elf_graph_kernel_count(elf_handle h);
 

@@ -1057,6 +1057,21 @@ int elf_get_stage_times(elf_handle h, float* ms, int max_stages) {
   return n;
 }
 
+int elf_get_stage_spans(elf_handle h, float* spans, int max_stages) {
+  if (int rc = check(h)) return rc;
+  if (!spans || max_stages < 0) return set_error(ELF_EINVAL, "bad output");
+  if (!h->tracing) return set_error(ELF_ESTATE, "tracing is off");
+  ELF_CK(cudaStreamSynchronize(h->user));
+  const int n = max_stages < ELF_NSTAGES ? max_stages : ELF_NSTAGES;
+  for (int i = 0; i < 2 * n; ++i) {
+    float t = -1.f;
+    if (cudaEventElapsedTime(&t, h->ev_stage[0], h->ev_stage[i]) != cudaSuccess) t = -1.f;
+    spans[i] = t;
+  }
+  cudaGetLastError();  // stages that never ran leave a benign "not ready" error behind
+  return n;
+}
+
 int elf_graph_kernel_count(elf_handle h) {
   if (int rc = check(h)) return rc;
   if (int rc = build_graph(h)) return rc;

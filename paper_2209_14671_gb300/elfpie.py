@@ -64,6 +64,7 @@ SIGNATURES = {
     "elf_get_weights": (c_int, [c_void_p, P_double, P_double]),
     "elf_set_tracing": (c_int, [c_void_p, c_int]),
     "elf_get_stage_times": (c_int, [c_void_p, P_float, c_int]),
+    "elf_get_stage_spans": (c_int, [c_void_p, P_float, c_int]),
     "elf_graph_kernel_count": (c_int, [c_void_p]),
     "elf_server_create": (c_int, [ctypes.c_size_t, c_int, ctypes.POINTER(c_void_p)]),
     "elf_server_submit": (c_int, [c_void_p, ctypes.POINTER(ElfProblem), ctypes.POINTER(ElfOptions), c_void_p, c_int,
@@ -308,6 +309,12 @@ class Elf:
         ms = (c_float * len(self.STAGES))()
         cnt = _check(load().elf_get_stage_times(self._h, ms, len(self.STAGES)), "elf_get_stage_times")
         return {self.STAGES[i]: float(ms[i]) for i in range(cnt)}
+
+    def stage_spans(self) -> dict:
+        """{stage: (start_ms, end_ms)} from the start of the most recent traced iteration (synchronises)."""
+        sp = (c_float * (2 * len(self.STAGES)))()
+        cnt = _check(load().elf_get_stage_spans(self._h, sp, len(self.STAGES)), "elf_get_stage_spans")
+        return {self.STAGES[i]: (float(sp[2 * i]), float(sp[2 * i + 1])) for i in range(cnt)}
 
     def kernels_per_step(self) -> int:
         return _check(load().elf_graph_kernel_count(self._h), "elf_graph_kernel_count")
