@@ -574,10 +574,11 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   h->rowsA = (h->nb + h->cs - 1) / h->cs;
   h->Q = pupil_chunks(K, S);
   h->hblocks = hess_blocks(N);
-  // gather lists (Eq. 9): for every spectrum row y and 32-pixel segment of it, the LEDs whose support
+  // gather lists (Eq. 9): for every spectrum row y and 64-pixel segment of it, the LEDs whose support
   // chord on that row crosses the segment, in ascending LED order, each as {LED, offset of the row
   // in the LED's compact G minus its first x, pupil index - x, first covered x | chord length << 16}
-  h->tiles_x = N / kGatherTile;
+  const int seg = gather_seg(N);
+  h->tiles_x = N / seg;
   std::vector<int> sptr((size_t)N * h->tiles_x + 1, 0);
   std::vector<int4> sent;
   {
@@ -588,7 +589,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
         if (cnt[jy] == 0) continue;
         const int y = oy + jy, lo = ox + xs[jy], hi = lo + cnt[jy];  // covered x in [lo, hi)
         const int4 e = make_int4(k, off[jy] - lo, jy * n - ox, lo | (cnt[jy] << 16));
-        for (int tx = lo / kGatherTile; tx <= (hi - 1) / kGatherTile; ++tx) lists[(size_t)y * h->tiles_x + tx].push_back(e);
+        for (int tx = lo / seg; tx <= (hi - 1) / seg; ++tx) lists[(size_t)y * h->tiles_x + tx].push_back(e);
       }
     }
     for (size_t i = 0; i < lists.size(); ++i) {

@@ -7,7 +7,8 @@
 
 namespace elf {
 
-constexpr int kGatherTile = 32;   // spectrum tile side of the gather lists
+constexpr int kGatherSeg = 64;    // row segment of the gather lists (two pixels per thread)
+inline int gather_seg(int N) { return N < kGatherSeg ? N : kGatherSeg; }
 constexpr int kCostRing = 4096;   // iterations kept in the cost ring buffer
 
 // ---------------------------------------------------------------- tile kernel

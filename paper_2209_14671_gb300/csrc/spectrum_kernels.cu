@@ -182,63 +182,77 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
   return d;
 }
 
-// One thread per spectrum pixel; a block covers 32 x 8 pixels, each warp one 32-pixel segment of a
-// row, whose list holds exactly the LEDs with a support chord crossing the segment (ascending).
+// Two horizontally adjacent spectrum pixels per thread (16-byte state loads and stores); the
+// threads of a row segment (64 pixels: one warp) walk that segment's list, which holds exactly the
+// LEDs whose support chord crosses it, in ascending order.
 __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
-  const int x = blockIdx.x * kGatherTile + threadIdx.x;
-  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int seg_w = 2 * blockDim.x;
+  const int x = blockIdx.x * seg_w + 2 * threadIdx.x;  // first of the thread's two pixels
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const size_t k = (size_t)y * a.N + x;
   const int seg = y * a.tiles_x + blockIdx.x;
   const int e0 = a.seg_ptr[seg], e1 = a.seg_ptr[seg + 1];
   // state loads first, so that they are in flight during the LED loop
-  float2 g = a.gH ? a.gH[k] : make_float2(0.f, 0.f);
-  float2 mu = make_float2(0.f, 0.f), ps = make_float2(0.f, 0.f);
-  float v = 0.f, dl = 0.f;
+  float4 g = a.gH ? *reinterpret_cast<const float4*>(a.gH + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 mu = make_float4(0.f, 0.f, 0.f, 0.f), ps = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 v = make_float2(0.f, 0.f), dl = make_float2(0.f, 0.f);
   if (a.mode == 0) {
-    mu = a.mu[k];
-    v = a.v[k];
-    dl = a.delta[k];
-    ps = a.psi[k];
+    mu = *reinterpret_cast<const float4*>(a.mu + k);
+    v = *reinterpret_cast<const float2*>(a.v + k);
+    dl = *reinterpret_cast<const float2*>(a.delta + k);
+    ps = *reinterpret_cast<const float4*>(a.psi + k);
   }
   // covering LEDs in ascending order; the loads of four entries are issued before their products
   // are added (same additions in the same order as one entry at a time)
-  float2 acc = make_float2(0.f, 0.f);
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
   constexpr int U = 4;
   for (int i0 = e0; i0 < e1; i0 += U) {
-    float2 p[U], gt[U];
-    bool ok[U];
+    float2 p0[U], g0[U], p1[U], g1[U];
+    bool ok0[U], ok1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      ok[u] = false;
-      p[u] = gt[u] = make_float2(0.f, 0.f);
+      ok0[u] = ok1[u] = false;
+      p0[u] = g0[u] = p1[u] = g1[u] = make_float2(0.f, 0.f);
       if (i0 + u < e1) {
-        const int4 e = __ldg(&a.seg_ent[i0 + u]);  // the same entry for the whole warp
+        const int4 e = __ldg(&a.seg_ent[i0 + u]);  // the same entry for the whole row segment
         const int lo = e.w & 0xffff, cnt = e.w >> 16;
+        const float2* gp = a.G + (size_t)e.x * a.S + e.y;
         if ((unsigned)(x - lo) < (unsigned)cnt) {
-          ok[u] = true;
-          p[u] = a.pupil[e.z + x];
-          gt[u] = a.G[(size_t)e.x * a.S + e.y + x];
+          ok0[u] = true;
+          p0[u] = a.pupil[e.z + x];
+          g0[u] = gp[x];
+        }
+        if ((unsigned)(x + 1 - lo) < (unsigned)cnt) {
+          ok1[u] = true;
+          p1[u] = a.pupil[e.z + x + 1];
+          g1[u] = gp[x + 1];
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (ok[u]) acc = cadd(acc, cconjmul(p[u], gt[u]));
+    for (int u = 0; u < U; ++u) {
+      if (ok0[u]) acc0 = cadd(acc0, cconjmul(p0[u], g0[u]));
+      if (ok1[u]) acc1 = cadd(acc1, cconjmul(p1[u], g1[u]));
+    }
   }
-  g = cadd(g, acc);
+  float2 ga = cadd(make_float2(g.x, g.y), acc0), gb = cadd(make_float2(g.z, g.w), acc1);
   if (a.mode == 1) {
-    a.g_out[k] = g;
+    *reinterpret_cast<float4*>(a.g_out + k) = make_float4(ga.x, ga.y, gb.x, gb.y);
     return;
   }
-  const float2 dlt = adabelief_step(g, mu, v, dl, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
-  a.psi_out[k] = csub(ps, dlt);
-  a.mu[k] = mu;
-  a.v[k] = v;
-  a.delta[k] = dl;
+  float2 mua = make_float2(mu.x, mu.y), mub = make_float2(mu.z, mu.w);
+  const float2 da = adabelief_step(ga, mua, v.x, dl.x, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
+  const float2 db = adabelief_step(gb, mub, v.y, dl.y, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
+  *reinterpret_cast<float4*>(a.psi_out + k) = make_float4(ps.x - da.x, ps.y - da.y, ps.z - db.x, ps.w - db.y);
+  *reinterpret_cast<float4*>(a.mu + k) = make_float4(mua.x, mua.y, mub.x, mub.y);
+  *reinterpret_cast<float2*>(a.v + k) = v;
+  *reinterpret_cast<float2*>(a.delta + k) = dl;
 }
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
-  dim3 grid(a.tiles_x, a.N / 8), block(32, 8);
+  const int seg = gather_seg(a.N);          // 64, or 32 for a 32 x 32 spectrum
+  const dim3 block(seg / 2, 256 / (seg / 2)); // one thread per two pixels of a segment
+  const dim3 grid(a.tiles_x, a.N / block.y);
   gather_kernel<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
