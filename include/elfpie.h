@@ -169,9 +169,9 @@ enum {
   ELF_STAGE_ITERATION = 0,     /* the whole iteration */
   ELF_STAGE_TILE = 1,          /* per-LED tile kernel (Eqs. 1, 5, 11, 12, F_B^H of Eq. 9) */
   ELF_STAGE_HESSIAN = 2,       /* O = F_A^-1 Psi, Eqs. 6-7, 13-14, F_A^H (second stream) */
-  ELF_STAGE_PUPIL_GRAD = 3,    /* Eq. 18 partial sums */
+  ELF_STAGE_PUPIL_GRAD = 3,    /* Eq. 18 partial sums; their last blocks apply Eq. 19 to P on the support */
   ELF_STAGE_GATHER = 4,        /* Eq. 9 gather fused with Eq. 19 for Psi */
-  ELF_STAGE_PUPIL_UPDATE = 5,  /* Gaussian filter + Eq. 19 for P */
+  ELF_STAGE_PUPIL_UPDATE = 5,  /* Eq. 19 for P off the support (gradient 0), from the iteration start */
   ELF_STAGE_COST = 6,          /* FP64 reduction of Eq. 8's terms */
   ELF_NSTAGES = 7
 };

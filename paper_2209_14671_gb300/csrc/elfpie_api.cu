@@ -95,6 +95,7 @@ struct elf_handle_s {
   float *v_p = nullptr, *delta_p = nullptr;
   // scratch
   float2 *G = nullptr, *ot = nullptr, *q = nullptr, *small = nullptr, *part = nullptr;
+  int* pdone = nullptr;  // per 256 support pixels: Eq. 18 chunks finished (reset by the partial kernel)
   float2 *psi_eval = nullptr, *pupil_eval = nullptr, *g_psi = nullptr, *g_p = nullptr, *pupil_unit = nullptr;
   float2* cost_ff = nullptr;  // per-warp (hi, lo) fidelity cost partials of the tile kernel
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
@@ -316,18 +317,20 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.g2 = (float)h->opt.gamma2;
   pa.eta = (float)h->opt.eta_opt;
   pa.mode = mode;
-  // the pupil chain (Eq. 18 partials, then the Eq. 19 update of P into pupil_next) on its own
-  // stream, beside the gather: the partials read Psi^t, which the gather leaves in place (it
-  // writes Psi^(t+1) into the other buffer)
+  // the pupil chain on its own stream, beside the gather: Eq. 19 off the support (no input from the
+  // tile kernel) from the start of the iteration, then the Eq. 18 partials, whose last blocks apply
+  // Eq. 19 on the support.  The partials read Psi^t, which the gather leaves in place (it writes
+  // Psi^(t+1) into the other buffer)
+  pa.done = h->pdone;
   if (pupil_path) {
+    ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_fork, 0));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 0);
+    ELF_CK(launch_pupil_offsupport(pa, h->paux));
+    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 1);
     ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_tile, 0));
     ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 0);
     ELF_CK(launch_pupil_partial(pa, h->paux));
     ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 1);
-    ELF_CK(cudaEventRecord(h->ev_pp, h->paux));
-    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 0);
-    ELF_CK(launch_pupil_update(pa, h->paux));
-    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 1);
     ELF_CK(cudaEventRecord(h->ev_pu, h->paux));
   }
 
@@ -659,6 +662,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->q, A))) return rc;
   if ((rc = dalloc(h, &h->small, B))) return rc;
   if ((rc = dalloc(h, &h->part, (size_t)h->Q * S))) return rc;
+  if ((rc = dalloc(h, &h->pdone, (size_t)(S + 255) / 256))) return rc;
+  ELF_CK(cudaMemset(h->pdone, 0, sizeof(int) * (size_t)((S + 255) / 256)));
   if ((rc = dalloc(h, &h->psi_eval, A))) return rc;
   if ((rc = dalloc(h, &h->pupil_eval, B))) return rc;
   if ((rc = dalloc(h, &h->g_psi, A))) return rc;

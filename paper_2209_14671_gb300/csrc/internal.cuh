@@ -132,6 +132,7 @@ struct PupilArgs {
   const float2* G; const float2* psi; const int2* origin;
   const int* sup_y; const int* sup_x; const int* sidx_map;   // S, S, n*n
   float2* part;           // Q x S
+  int* done;              // ceil(S / 256) counters of finished chunks, zero between launches
   const float2* pupil;    // P^t
   float2* pupil_next;     // P^{t+1}
   float2* mu; float* v; float* delta;
@@ -144,7 +145,7 @@ struct PupilArgs {
 };
 int pupil_chunks(int K, int S);
 cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s);
-cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s);
+cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,

@@ -266,56 +266,14 @@ int pupil_chunks(int K, int S) {
   return q;
 }
 
-__global__ void __launch_bounds__(256) pupil_partial_kernel(const PupilArgs a) {
-  const int s = blockIdx.x * 256 + threadIdx.x;
-  if (s >= a.S) return;
-  const int q = blockIdx.y;
-  const int kc = (a.K + a.Q - 1) / a.Q;
-  const int k0 = q * kc, k1 = min(a.K, k0 + kc);
-  const int jy = a.sup_y[s], jx = a.sup_x[s];
-  // LEDs in ascending order; four at a time have their loads in flight together
-  float2 acc = make_float2(0.f, 0.f);
-  constexpr int U = 4;
-  for (int k = k0; k < k1; k += U) {
-    float2 ps[U], gt[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      ps[u] = gt[u] = make_float2(0.f, 0.f);
-      if (k + u < k1) {
-        const int2 o = a.origin[k + u];
-        ps[u] = a.psi[(size_t)(o.x + jy) * a.N + o.y + jx];
-        gt[u] = a.G[(size_t)(k + u) * a.S + s];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (k + u < k1) acc = cadd(acc, cconjmul(ps[u], gt[u]));
-  }
-  a.part[(size_t)q * a.S + s] = acc;
-}
-
-__global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
-  const int j = blockIdx.x * 256 + threadIdx.x;
-  const int n = a.n;
-  if (j >= n * n) return;
-  const int sidx = a.sidx_map[j];
-  float2 g = make_float2(0.f, 0.f);
-  if (sidx >= 0) {
-    constexpr int U = 8;  // loads of eight chunks in flight, added in chunk order
-    for (int q0 = 0; q0 < a.Q; q0 += U) {
-      float2 pv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        pv[u] = (q0 + u < a.Q) ? a.part[(size_t)(q0 + u) * a.S + sidx] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q0 + u < a.Q) g = cadd(g, pv[u]);
-    }
-  }
+// Eq. 19 for one pupil pixel j with gradient g (zero off the support): the 3x3 Gaussian of P^t
+// (note under Algorithm 1) as the base, P^(t+1) = mask o (base - Delta); gradient mode writes g.
+__device__ __forceinline__ void pupil_update_pixel(const PupilArgs& a, int j, float2 g, bool on_support) {
   if (a.mode == 1) {
     a.g_out[j] = g;
     return;
   }
+  const int n = a.n;
   const int jy = j / n, jx = j - jy * n;
   float2 base;
   if (a.filter) {
@@ -339,7 +297,69 @@ __global__ void __launch_bounds__(256) pupil_update_kernel(const PupilArgs a) {
   a.mu[j] = mu;
   a.v[j] = v;
   a.delta[j] = dl;
-  a.pupil_next[j] = (sidx >= 0) ? csub(base, d) : make_float2(0.f, 0.f);
+  a.pupil_next[j] = on_support ? csub(base, d) : make_float2(0.f, 0.f);
+}
+
+// Eq. 18 in LED chunks: block (x, q) sums chunk q's LEDs for 256 support pixels.  The last block of
+// each column of blocks to finish (a counter per column, reset by that block) then sums the Q
+// partials of its pixels in chunk order and applies Eq. 19: no second launch, and the same sums in
+// the same order whichever block is last.
+__global__ void __launch_bounds__(256) pupil_partial_kernel(const PupilArgs a) {
+  __shared__ int last;
+  const int s = blockIdx.x * 256 + threadIdx.x;
+  const bool valid = s < a.S;
+  const int q = blockIdx.y;
+  const int kc = (a.K + a.Q - 1) / a.Q;
+  const int k0 = q * kc, k1 = min(a.K, k0 + kc);
+  const int jy = valid ? a.sup_y[s] : 0, jx = valid ? a.sup_x[s] : 0;
+  // LEDs in ascending order; four at a time have their loads in flight together
+  float2 acc = make_float2(0.f, 0.f);
+  constexpr int U = 4;
+  for (int k = k0; valid && k < k1; k += U) {
+    float2 ps[U], gt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ps[u] = gt[u] = make_float2(0.f, 0.f);
+      if (k + u < k1) {
+        const int2 o = a.origin[k + u];
+        ps[u] = a.psi[(size_t)(o.x + jy) * a.N + o.y + jx];
+        gt[u] = a.G[(size_t)(k + u) * a.S + s];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k + u < k1) acc = cadd(acc, cconjmul(ps[u], gt[u]));
+  }
+  if (valid) a.part[(size_t)q * a.S + s] = acc;
+  __threadfence();  // the partial is visible device-wide before this block is counted
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&a.done[blockIdx.x], 1) == a.Q - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (valid) {
+    float2 g = make_float2(0.f, 0.f);
+    constexpr int V = 8;  // loads of eight chunks in flight, added in chunk order
+    for (int q0 = 0; q0 < a.Q; q0 += V) {
+      float2 pv[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        pv[u] = (q0 + u < a.Q) ? __ldcg(&a.part[(size_t)(q0 + u) * a.S + s]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        if (q0 + u < a.Q) g = cadd(g, pv[u]);
+    }
+    pupil_update_pixel(a, jy * a.n + jx, g, true);
+  }
+  if (threadIdx.x == 0) a.done[blockIdx.x] = 0;  // ready for the next launch
+}
+
+// Eq. 19 for the pixels off the support (gradient 0; P^(t+1) = 0 there): needs nothing from the
+// tile kernel, so it runs at the start of the pupil chain.
+__global__ void __launch_bounds__(256) pupil_offsupport_kernel(const PupilArgs a) {
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= a.n * a.n || a.sidx_map[j] >= 0) return;
+  pupil_update_pixel(a, j, make_float2(0.f, 0.f), false);
 }
 
 cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s) {
@@ -348,8 +368,8 @@ cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pupil_update(const PupilArgs& a, cudaStream_t s) {
-  pupil_update_kernel<<<(a.n * a.n + 255) / 256, 256, 0, s>>>(a);
+cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s) {
+  pupil_offsupport_kernel<<<(a.n * a.n + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
