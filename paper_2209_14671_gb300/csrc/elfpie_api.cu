@@ -190,6 +190,42 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
   ELF_CK(cudaEventRecord(h->ev_join, h->aux));
 
+  PupilArgs pa{};
+  pa.G = h->G;
+  pa.psi = psi;
+  pa.origin = h->origin;
+  pa.sup_y = h->sup_y;
+  pa.sup_x = h->sup_x;
+  pa.sidx_map = h->sidx_map;
+  pa.part = h->part;
+  pa.pupil = pupil;
+  pa.pupil_next = pupil_out;
+  pa.mu = h->mu_p;
+  pa.v = h->v_p;
+  pa.delta = h->delta_p;
+  pa.g_out = h->g_p;
+  pa.bc = h->bc;
+  pa.N = h->N;
+  pa.n = h->n;
+  pa.S = h->S;
+  pa.K = h->K;
+  pa.Q = h->Q;
+  pa.filter = h->opt.pupil_filter;
+  pa.w0 = h->gw0;
+  pa.w1 = h->gw1;
+  pa.g1 = (float)h->opt.gamma1;
+  pa.g2 = (float)h->opt.gamma2;
+  pa.eta = (float)h->opt.eta_opt;
+  pa.mode = mode;
+  pa.done = h->pdone;
+  // Eq. 19 off the support (gradient 0) needs nothing from the tile kernel: it runs on the auxiliary
+  // stream after the Hessian branch, on the SMs the tile clusters leave free
+  if (pupil_path) {
+    ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 0);
+    ELF_CK(launch_pupil_offsupport(pa, h->aux));
+    ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 1);
+  }
+
   // tile path: Eqs. 1, 5 (4), 12, 11 (10) and F_B^H of Eq. 9
   TileArgs ta{};
   ta.psi = psi;
@@ -290,43 +326,11 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_MARK(h->aux, ELF_STAGE_COST, 1);
   ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
 
-  PupilArgs pa{};
-  pa.G = h->G;
-  pa.psi = psi;
-  pa.origin = h->origin;
-  pa.sup_y = h->sup_y;
-  pa.sup_x = h->sup_x;
-  pa.sidx_map = h->sidx_map;
-  pa.part = h->part;
-  pa.pupil = pupil;
-  pa.pupil_next = pupil_out;
-  pa.mu = h->mu_p;
-  pa.v = h->v_p;
-  pa.delta = h->delta_p;
-  pa.g_out = h->g_p;
-  pa.bc = h->bc;
-  pa.N = h->N;
-  pa.n = h->n;
-  pa.S = h->S;
-  pa.K = h->K;
-  pa.Q = h->Q;
-  pa.filter = h->opt.pupil_filter;
-  pa.w0 = h->gw0;
-  pa.w1 = h->gw1;
-  pa.g1 = (float)h->opt.gamma1;
-  pa.g2 = (float)h->opt.gamma2;
-  pa.eta = (float)h->opt.eta_opt;
-  pa.mode = mode;
-  // the pupil chain on its own stream, beside the gather: Eq. 19 off the support (no input from the
-  // tile kernel) from the start of the iteration, then the Eq. 18 partials, whose last blocks apply
-  // Eq. 19 on the support.  The partials read Psi^t, which the gather leaves in place (it writes
+  // the pupil chain on its own stream, beside the gather: the Eq. 18 partials, whose last blocks
+  // apply Eq. 19 on the support (Eq. 19 off the support ran on the auxiliary stream after the
+  // Hessian branch).  The partials read Psi^t, which the gather leaves in place (it writes
   // Psi^(t+1) into the other buffer)
-  pa.done = h->pdone;
   if (pupil_path) {
-    ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_fork, 0));
-    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 0);
-    ELF_CK(launch_pupil_offsupport(pa, h->paux));
-    ELF_MARK(h->paux, ELF_STAGE_PUPIL_UPDATE, 1);
     ELF_CK(cudaStreamWaitEvent(h->paux, h->ev_tile, 0));
     ELF_MARK(h->paux, ELF_STAGE_PUPIL_GRAD, 0);
     ELF_CK(launch_pupil_partial(pa, h->paux));

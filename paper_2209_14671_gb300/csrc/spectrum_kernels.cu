@@ -185,27 +185,18 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
 // Two horizontally adjacent spectrum pixels per thread (16-byte state loads and stores); the
 // threads of a row segment (64 pixels: one warp) walk that segment's list, which holds exactly the
 // LEDs whose support chord crosses it, in ascending order.
-__global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
+__global__ void __launch_bounds__(256, 6) gather_kernel(const GatherArgs a) {
   const int seg_w = 2 * blockDim.x;
   const int x = blockIdx.x * seg_w + 2 * threadIdx.x;  // first of the thread's two pixels
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const size_t k = (size_t)y * a.N + x;
   const int seg = y * a.tiles_x + blockIdx.x;
   const int e0 = a.seg_ptr[seg], e1 = a.seg_ptr[seg + 1];
-  // state loads first, so that they are in flight during the LED loop
-  float4 g = a.gH ? *reinterpret_cast<const float4*>(a.gH + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 mu = make_float4(0.f, 0.f, 0.f, 0.f), ps = make_float4(0.f, 0.f, 0.f, 0.f);
-  float2 v = make_float2(0.f, 0.f), dl = make_float2(0.f, 0.f);
-  if (a.mode == 0) {
-    mu = *reinterpret_cast<const float4*>(a.mu + k);
-    v = *reinterpret_cast<const float2*>(a.v + k);
-    dl = *reinterpret_cast<const float2*>(a.delta + k);
-    ps = *reinterpret_cast<const float4*>(a.psi + k);
-  }
-  // covering LEDs in ascending order; the loads of four entries are issued before their products
-  // are added (same additions in the same order as one entry at a time)
+  // covering LEDs in ascending order; the loads of two entries are issued before their products
+  // are added (same additions in the same order as one entry at a time).  Few loads in flight per
+  // thread and 38 registers: six blocks per SM, whose warps hide the latency
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-  constexpr int U = 4;
+  constexpr int U = 2;
   for (int i0 = e0; i0 < e1; i0 += U) {
     float2 p0[U], g0[U], p1[U], g1[U];
     bool ok0[U], ok1[U];
@@ -234,6 +225,17 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
       if (ok0[u]) acc0 = cadd(acc0, cconjmul(p0[u], g0[u]));
       if (ok1[u]) acc1 = cadd(acc1, cconjmul(p1[u], g1[u]));
     }
+  }
+  // the state after the LED loop, so that the loop's loads and the state do not hold registers at the
+  // same time (occupancy hides the latency instead)
+  const float4 g = a.gH ? *reinterpret_cast<const float4*>(a.gH + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 mu = make_float4(0.f, 0.f, 0.f, 0.f), ps = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 v = make_float2(0.f, 0.f), dl = make_float2(0.f, 0.f);
+  if (a.mode == 0) {
+    mu = *reinterpret_cast<const float4*>(a.mu + k);
+    v = *reinterpret_cast<const float2*>(a.v + k);
+    dl = *reinterpret_cast<const float2*>(a.delta + k);
+    ps = *reinterpret_cast<const float4*>(a.psi + k);
   }
   float2 ga = cadd(make_float2(g.x, g.y), acc0), gb = cadd(make_float2(g.z, g.w), acc1);
   if (a.mode == 1) {
