@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-fidelity", action="store_true", help="skip the fidelity-variant leg")
     ap.add_argument("--no-mux", action="store_true", help="skip the multiplexed-illumination leg")
     ap.add_argument("--no-eval", action="store_true", help="skip the evaluation leg (Eqs. 20-22)")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other-workload throughput leg")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the mixed serving stream (0 disables the serving leg)")
     return ap.parse_args()
@@ -369,6 +370,31 @@ def eval_leg(wid, w, I_dev, obj_dev, torch, dev):
                     "(its images are not available)"}
 
 
+def workloads_leg(torch, dev, steps=50, warmup=5):
+    """Throughput of the other two workloads (not the headline): the 64 x 64 / 49-LED / 256 x 256
+    problem and the 128 x 128 / 225-LED / 512 x 512 problem, each timed over `steps` iterations with
+    CUDA events on its stream after `warmup` iterations (inputs resident, L2 not flushed: these
+    problems fit in L2)."""
+    from paper_2209_14671_gb300 import elfpie as E
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for wid in (0, 3):
+        w = IN.problem(wid)
+        I = torch.from_numpy(make_inputs(w, wid, torch, dev)).to(dev)
+        with E.Elf(w["n"], w["u"], w["k_xy"], w["na"], w["wavelength_um"], w["pixel_um"], stream=stream) as elf:
+            elf.set_measurements(I)
+            elf.step(warmup)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            s0.record(stream)
+            elf.step(steps)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = s0.elapsed_time(s1) / steps
+        out[w["name"]] = {"ms_per_iteration": ms, "led_updates_per_s": w["K"] / (ms * 1e-3)}
+    return out
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -517,6 +543,10 @@ def run_ours(args):
     if not args.no_fidelity and world == 1:
         fidelity = fidelity_leg(w, I_dev, torch, dev)
 
+    workloads = None
+    if not args.no_workloads and world == 1:
+        workloads = workloads_leg(torch, dev)
+
     evaluation = None
     if not args.no_eval and world == 1:
         obj = torch.from_numpy(IN.object_field(wid, w).astype(np.complex64)).to(dev)
@@ -566,6 +596,7 @@ def run_ours(args):
             "fidelity_variants": fidelity,
             "multiplexed": mux,
             "evaluation": evaluation,
+            "other_workloads": workloads,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
