@@ -63,6 +63,7 @@ struct elf_handle_s {
   int graph_kernels = 0;
   cudaEvent_t ev_stage[2 * ELF_NSTAGES] = {};
   cudaGraphExec_t graph[2] = {};  // iteration from psi_buf[p] into psi_buf[p ^ 1]
+  cudaGraphExec_t graph_r[2] = {};  // kGraphIters iterations from buffer p back to buffer p (untraced)
   std::vector<int2> origin_h;
   std::vector<int> sidx_h;  // linear support indices in compact order
   float gw0 = 0.f, gw1 = 0.f;
@@ -376,48 +377,65 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   return ELF_OK;
 }
 
-int build_graph(elf_handle h) {
-  if (h->graph[0] && h->graph[1]) return ELF_OK;
-  for (int p = 0; p < 2; ++p) {
-    if (h->graph[p]) continue;
-    cudaGraph_t g = nullptr;
-    ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    const bool lp = h->opt.learn_pupil != 0;
-    int rc = enqueue_iteration(h, 0, h->cap, h->psi_buf[p], h->pupil_buf[lp ? p : 0], h->psi_buf[p ^ 1],
-                               lp ? h->pupil_buf[p ^ 1] : nullptr);
-    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-    if (rc != ELF_OK) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+// Captures `iters` iterations starting from buffer p into one executable graph.
+int capture_iterations(elf_handle h, int p, int iters, cudaGraphExec_t* out, int* kernels) {
+  cudaGraph_t g = nullptr;
+  ELF_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  const bool lp = h->opt.learn_pupil != 0;
+  int rc = ELF_OK;
+  for (int i = 0; i < iters && rc == ELF_OK; ++i) {
+    const int q = p ^ (i & 1);  // buffers alternate iteration by iteration
+    rc = enqueue_iteration(h, 0, h->cap, h->psi_buf[q], h->pupil_buf[lp ? q : 0], h->psi_buf[q ^ 1],
+                           lp ? h->pupil_buf[q ^ 1] : nullptr);
+  }
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (rc != ELF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return set_error(ELF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (kernels) {
     size_t nn = 0;
-    h->graph_kernels = 0;
+    *kernels = 0;
     if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
       std::vector<cudaGraphNode_t> nodes(nn);
       if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
         for (size_t i = 0; i < nn; ++i) {
           cudaGraphNodeType t;
-          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++*kernels;
         }
     }
-    // per-node priorities: the Hessian branch was captured from the high-priority stream
-    e = cudaGraphInstantiateWithFlags(&h->graph[p], g, cudaGraphInstantiateFlagUseNodePriority);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      h->graph[p] = nullptr;
-      return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
+  }
+  // per-node priorities: the Hessian branch was captured from the high-priority stream
+  e = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return set_error(ELF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return ELF_OK;
+}
+
+// Single-iteration graphs for both buffer parities and, when tracing is off, graphs of kGraphIters
+// iterations (an even count: they return to the parity they start from), which save the launch gaps
+// between iterations on small problems.
+int build_graph(elf_handle h) {
+  for (int p = 0; p < 2; ++p) {
+    if (!h->graph[p])
+      if (int rc = capture_iterations(h, p, 1, &h->graph[p], &h->graph_kernels)) return rc;
+    if (!h->tracing && !h->graph_r[p])
+      if (int rc = capture_iterations(h, p, kGraphIters, &h->graph_r[p], nullptr)) return rc;
   }
   return ELF_OK;
 }
 
 void destroy_graphs(elf_handle h) {
-  for (cudaGraphExec_t& g : h->graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (cudaGraphExec_t* set : {h->graph, h->graph_r})
+    for (int p = 0; p < 2; ++p)
+      if (set[p]) {
+        cudaGraphExecDestroy(set[p]);
+        set[p] = nullptr;
+      }
 }
 
 // Makes buffer 0 of Psi and P current (before writing a new state into them).
@@ -829,6 +847,8 @@ int elf_step(elf_handle h, int n_iter) {
   if (!h->have_meas) return set_error(ELF_ESTATE, "elf_step before elf_set_measurements");
   if (n_iter < 0) return set_error(ELF_EINVAL, "negative n_iter");
   if (int rc = build_graph(h)) return rc;
+  for (; !h->tracing && n_iter >= kGraphIters; n_iter -= kGraphIters)
+    ELF_CK(cudaGraphLaunch(h->graph_r[h->cur], h->user));  // even count: the parity is unchanged
   for (int i = 0; i < n_iter; ++i) {
     ELF_CK(cudaGraphLaunch(h->graph[h->cur], h->user));
     h->cur ^= 1;  // the iteration's Psi^(t+1) and P^(t+1) are in the other buffers
@@ -1044,7 +1064,7 @@ int elf_get_weights(elf_handle h, double* alpha, double* beta) {
 int elf_set_tracing(elf_handle h, int enable) {
   if (int rc = check(h)) return rc;
   const bool en = enable != 0;
-  if (en != h->tracing && (h->graph[0] || h->graph[1])) {
+  if (en != h->tracing) {
     ELF_CK(cudaStreamSynchronize(h->user));
     destroy_graphs(h);
   }

@@ -10,6 +10,7 @@ namespace elf {
 constexpr int kGatherSeg = 64;    // row segment of the gather lists (two pixels per thread)
 inline int gather_seg(int N) { return N < kGatherSeg ? N : kGatherSeg; }
 constexpr int kCostRing = 4096;   // iterations kept in the cost ring buffer
+constexpr int kGraphIters = 8;    // iterations per graph launch of elf_step when tracing is off (even)
 
 // ---------------------------------------------------------------- tile kernel
 // One cluster of CS CTAs per LED runs Eqs. 1, 5/4, 12, 11/10 and F_B^H of Eq. 9.
