@@ -56,7 +56,7 @@ struct elf_handle_s {
   double pupil_cut = 0.0;  // NA / lambda, the pupil radius in cycles/um
   elf_options opt{};
   cudaStream_t user = nullptr, cap = nullptr, aux = nullptr, paux = nullptr;  // paux: pupil chain
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr, ev_pp = nullptr,
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tile = nullptr, ev_cost = nullptr,
               ev_pu = nullptr;
   bool have_meas = false;
   bool tracing = false;
@@ -505,7 +505,6 @@ void elf_destroy(elf_handle h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_tile) cudaEventDestroy(h->ev_tile);
   if (h->ev_cost) cudaEventDestroy(h->ev_cost);
-  if (h->ev_pp) cudaEventDestroy(h->ev_pp);
   if (h->ev_pu) cudaEventDestroy(h->ev_pu);
   if (h->paux) cudaStreamDestroy(h->paux);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -640,7 +639,6 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   ELF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_tile, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_cost, cudaEventDisableTiming));
-  ELF_CK(cudaEventCreateWithFlags(&h->ev_pp, cudaEventDisableTiming));
   ELF_CK(cudaEventCreateWithFlags(&h->ev_pu, cudaEventDisableTiming));
   ELF_CK(cudaStreamCreateWithPriority(&h->paux, cudaStreamNonBlocking, prio_high));  // short pupil kernels first
   for (cudaEvent_t& ev : h->ev_stage) ELF_CK(cudaEventCreate(&ev));

@@ -55,6 +55,8 @@ def case(name: str) -> dict:
         return _tiny(32, 4, 5, 5, 7.5, 2)
     if name == "single_led":
         return _tiny(32, 2, 1, 0, 6.0, 3)
+    if name == "nou32":  # no upsampling (u = 1): the one LED's crop is the whole spectrum
+        return _tiny(32, 1, 1, 0, 6.0, 5)
     if name == "wide256":  # n = 256 with a pupil band of 231 rows: the widest tile-kernel shared memory layout
         return _tiny(256, 2, 3, 40, 115.0, 4)
     if name.startswith("w"):

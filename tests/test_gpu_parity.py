@@ -25,7 +25,7 @@ from _cases import case, load_state, oracle_state_to_f32, rel
 
 pytestmark = pytest.mark.gpu
 
-CASES = ["tiny16", "single_led", "small32", "w0", "w3", "w1", "wide256"]
+CASES = ["tiny16", "single_led", "nou32", "small32", "w0", "w3", "w1", "wide256"]
 
 TOL_FWD = 1e-5
 TOL_GRAD = 2e-3
