@@ -316,11 +316,11 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_MARK(h->aux, ELF_STAGE_COST, 0);
   {
     // fidelity partials: FP64 per LED (tensor-core path), per image block (multiplexed images), or
-    // the tile kernel's per-warp pairs
+    // the tile kernel's per-CTA pairs
     const bool tc = h->opt.tile_dft != 0, mx = h->mux > 1;
     const double* fid = mx ? h->mux_cost : h->cost_fid;
     const int nfid = tc ? h->K : (mx ? h->n_img * mux_blocks_per_image(h->n) : 0);
-    ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs * tile_warps(h->n), h->cost_h,
+    ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs, h->cost_h,
                               h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out3 : nullptr,
                               h->aux));
   }

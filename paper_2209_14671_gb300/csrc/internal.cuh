@@ -24,7 +24,7 @@ struct TileArgs {
   const int* row_off;     // n: compact index of the first support pixel of each row
   const float2* tw;       // n team twiddles tw[k1 * Q + l] = e^{-2 pi i l k1 / n}
   float2* G;              // K x S tile gradients on the support (gradient mode)
-  float2* cost_ff;        // K x CS x warps fidelity cost partials, (hi, lo) float pairs
+  float2* cost_ff;        // K x CS fidelity cost partials (one per CTA), (hi, lo) float pairs
   int* err;               // set to 1 when a bounded wait of a DSMEM exchange ran out
   float* I_out;           // K x n x n predicted intensities (simulate mode)
   int N, K, S, Blo, nb, rowsA;

@@ -185,7 +185,7 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
 // Two horizontally adjacent spectrum pixels per thread (16-byte state loads and stores); the
 // threads of a row segment (64 pixels: one warp) walk that segment's list, which holds exactly the
 // LEDs whose support chord crosses it, in ascending order.
-__global__ void __launch_bounds__(256, 6) gather_kernel(const GatherArgs a) {
+__global__ void __launch_bounds__(256, 5) gather_kernel(const GatherArgs a) {
   const int seg_w = 2 * blockDim.x;
   const int x = blockIdx.x * seg_w + 2 * threadIdx.x;  // first of the thread's two pixels
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -194,18 +194,34 @@ __global__ void __launch_bounds__(256, 6) gather_kernel(const GatherArgs a) {
   const int e0 = a.seg_ptr[seg], e1 = a.seg_ptr[seg + 1];
   // covering LEDs in ascending order; the loads of two entries are issued before their products
   // are added (same additions in the same order as one entry at a time).  Few loads in flight per
-  // thread and 38 registers: six blocks per SM, whose warps hide the latency
+  // thread and 47 registers: five blocks per SM, whose warps hide the latency
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
   constexpr int U = 2;
-  for (int i0 = e0; i0 < e1; i0 += U) {
+  // the segment's entries, 32 at a time, one per lane, handed round by shuffles: only the G and
+  // pupil loads of a round wait on memory (a warp is one row segment when the segment has 64 pixels;
+  // with 32-pixel segments two rows share a warp and each half-warp shuffles within itself)
+  const int lanes = min((int)blockDim.x, 32);
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int lane_base = lane & ~(lanes - 1);
+  const unsigned wmask = (lanes == 32) ? 0xffffffffu : (0xffffu << lane_base);
+  for (int c0 = e0; c0 < e1; c0 += lanes) {
+    const int cl = lane - lane_base;
+    const int4 mine = (c0 + cl < e1) ? __ldg(&a.seg_ent[c0 + cl]) : make_int4(0, 0, 0, 0);
+    const int c1 = min(e1, c0 + lanes);
+  for (int i0 = c0; i0 < c1; i0 += U) {
     float2 p0[U], g0[U], p1[U], g1[U];
     bool ok0[U], ok1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ok0[u] = ok1[u] = false;
       p0[u] = g0[u] = p1[u] = g1[u] = make_float2(0.f, 0.f);
-      if (i0 + u < e1) {
-        const int4 e = __ldg(&a.seg_ent[i0 + u]);  // the same entry for the whole row segment
+      const int src = lane_base + min(i0 + u - c0, lanes - 1);
+      int4 e;
+      e.x = __shfl_sync(wmask, mine.x, src);
+      e.y = __shfl_sync(wmask, mine.y, src);
+      e.z = __shfl_sync(wmask, mine.z, src);
+      e.w = __shfl_sync(wmask, mine.w, src);
+      if (i0 + u < c1) {
         const int lo = e.w & 0xffff, cnt = e.w >> 16;
         const float2* gp = a.G + (size_t)e.x * a.S + e.y;
         if ((unsigned)(x - lo) < (unsigned)cnt) {
@@ -225,6 +241,7 @@ __global__ void __launch_bounds__(256, 6) gather_kernel(const GatherArgs a) {
       if (ok0[u]) acc0 = cadd(acc0, cconjmul(p0[u], g0[u]));
       if (ok1[u]) acc1 = cadd(acc1, cconjmul(p1[u], g1[u]));
     }
+  }
   }
   // the state after the LED loop, so that the loop's loads and the state do not hold registers at the
   // same time (occupancy hides the latency instead)

@@ -434,12 +434,19 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       }
     }
   }  // mode 2 leaves acc = 0: the cost pairs of its LEDs are zero
-  // the warp's cost pair, summed in a fixed order with the other warps' by the cost reduction
+  // the warps' cost pairs, summed in warp order by the last warp (idle in the stencil and in the
+  // forward column transforms) into one pair per CTA for the cost reduction
+  float2* cpair = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Hx + 2 * NL) + 16);
   {
     const FF wsum = warp_sum_ff(FF{acc, 0.f});
-    if (wl == 0) a.cost_ff[((size_t)led * CS + crank) * NW + warp] = make_float2(wsum.hi, wsum.lo);
+    if (wl == 0) cpair[warp] = make_float2(wsum.hi, wsum.lo);
   }
   __syncthreads();  // W is complete in every column before the column transforms read it
+  if (tid == NT - 32) {
+    FF s = {cpair[0].x, cpair[0].y};
+    for (int w = 1; w < NW; ++w) s = ff_add(s, FF{cpair[w].x, cpair[w].y});
+    a.cost_ff[(size_t)led * CS + crank] = make_float2(s.hi, s.lo);
+  }
 
   // forward column transforms of the owned columns (only the support band rows of the output are
   // written back: the other rows are never read), then push the band rows to their owners
@@ -535,7 +542,7 @@ size_t tile_smem_bytes(int n, int cs, int rowsA) {
   const size_t rp = fft_padded_length(n);
   const size_t cw = n / cs;
   return 4 * (size_t)n * (cw + 2) + 8 * ((size_t)n + (size_t)rowsA * rp + rp * (size_t)oc_pitch(n)) +
-         4 * 2 * (size_t)n + 16;  // ... + Hx + two mbarriers
+         4 * 2 * (size_t)n + 16 + 8 * (size_t)tile_warps(n);  // ... + Hx + two mbarriers + cost pairs
 }
 
 int tile_warps(int n) { return tile_threads(n) / 32; }
