@@ -434,20 +434,14 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
       }
     }
   }  // mode 2 leaves acc = 0: the cost pairs of its LEDs are zero
-  // the warps' cost pairs, summed in warp order by the last warp (idle in the stencil and in the
-  // forward column transforms) into one pair per CTA for the cost reduction
+  // the warps' cost pairs, summed in warp order by the last warp into one pair per CTA for the cost
+  // reduction (below, after that warp's pushes)
   float2* cpair = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Hx + 2 * NL) + 16);
   {
     const FF wsum = warp_sum_ff(FF{acc, 0.f});
     if (wl == 0) cpair[warp] = make_float2(wsum.hi, wsum.lo);
   }
   __syncthreads();  // W is complete in every column before the column transforms read it
-  if (tid == NT - 32) {
-    FF s = {cpair[0].x, cpair[0].y};
-    for (int w = 1; w < NW; ++w) s = ff_add(s, FF{cpair[w].x, cpair[w].y});
-    a.cost_ff[(size_t)led * CS + crank] = make_float2(s.hi, s.lo);
-  }
-
   // forward column transforms of the owned columns (only the support band rows of the output are
   // written back: the other rows are never read), then push the band rows to their owners
   for (int base = 0; base < CW; base += NTEAM) {
@@ -484,6 +478,13 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         *dst = OC[py * PO + cc + 1];
       }
     }
+  }
+  // the CTA's cost pair: the warps' pairs summed in warp order by the last warp, after its pushes and
+  // while the exchange completes
+  if (tid == NT - 32) {
+    FF s = {cpair[0].x, cpair[0].y};
+    for (int w = 1; w < NW; ++w) s = ff_add(s, FF{cpair[w].x, cpair[w].y});
+    a.cost_ff[(size_t)led * CS + crank] = make_float2(s.hi, s.lo);
   }
   if constexpr (CS > 1) {
     mbar_wait_or_flag(&mbar[1], a.err);  // all n columns of this CTA's band rows have landed
