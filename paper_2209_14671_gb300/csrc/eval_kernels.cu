@@ -293,6 +293,8 @@ extern "C" int elf_degrade(elf_handle h, const float* I_clean, const float* zeta
     return elf::handle_set_error(ELF_EINVAL, "elf_degrade: need 0 <= illum_c <= 1, finite gauss_a, 0 <= density <= 1");
   if ((c != 0 && (!zeta || !(w > 0 && std::isfinite(w)))) || (a != 0 && !xi) || (d != 0 && !u_snp))
     return elf::handle_set_error(ELF_EINVAL, "elf_degrade: a random field or the waist is missing");
+  if (I_out == I_clean || I_out == zeta || I_out == xi || I_out == u_snp)
+    return elf::handle_set_error(ELF_EINVAL, "elf_degrade: I_out must not alias an input");
   int n = 0, N = 0, n_img = 0;
   elf::handle_image_info(h, &n, &N, &n_img);
   if (n > elf::kBlurMax) return elf::handle_set_error(ELF_EINVAL, "elf_degrade: image side too large");

@@ -124,3 +124,6 @@ def test_degrade_validates_its_arguments():
             with pytest.raises(E.ElfError) as ei:
                 elf.degrade(I0, out, **kw)
             assert ei.value.code == E.ELF_EINVAL
+        with pytest.raises(E.ElfError) as ei:  # the output may not alias an input
+            elf.degrade(I0, I0, gauss_a=0.1, xi=out)
+        assert ei.value.code == E.ELF_EINVAL
