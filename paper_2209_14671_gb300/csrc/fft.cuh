@@ -232,59 +232,4 @@ __device__ __forceinline__ void team_fft(float2* buf, const float2* __restrict__
   team_fft_regs<L, INV, S>(v, buf, tw, lane, active);
 }
 
-
-// A 256-point transform owned by a whole warp (32 lanes, 8 values each), for rows processed while
-// most of the block has no transform to do: half the per-lane work and latency of a 16-lane team.
-// Same decomposition, twiddle table and transpose layout as FftTeam<256> (P = Q = 16):
-//   pass 1  lane (c, h) = (lane / 2, lane % 2) holds x[c + 16 j] for the j = 2 i + h of its parity;
-//           an 8-point DFT over i gives the even (h = 0) or odd (h = 1) half of the 16-point DFT
-//           over j, which the two lanes of a pair combine by shuffles: lane h keeps the outputs
-//           k1 = 8 h .. 8 h + 7; then the twiddle W_256^(c k1) and the transposed store at k1 * 17 + c;
-//   pass 2  lane (k1, h) loads row k1 at columns c = 2 i + h, same split, and ends with
-//           X[k1 + 16 k2] for k2 = 8 h + m in v[m].
-// On entry v[i] = x[(lane / 2) + 16 (2 i + lane % 2)]; buf holds 272 elements (scratch).
-template <bool INV>
-__device__ __forceinline__ void warp_fft256_half(float2 (&v)[8], int h) {
-  Dft<8, INV>::run(v);
-  float2 o[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    o[m].x = __shfl_xor_sync(0xffffffffu, v[m].x, 1);
-    o[m].y = __shfl_xor_sync(0xffffffffu, v[m].y, 1);
-  }
-  // X[m] = E[m] + W16^m O[m], X[m + 8] = E[m] - W16^m O[m]; lane h = 0 holds E, lane h = 1 holds O
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const float2 e = h ? o[m] : v[m];
-    const float2 od = h ? v[m] : o[m];
-    const float2 t = twmul<INV>(od, 2 * m);  // W_32^(2m) = W_16^m
-    v[m] = h ? csub(e, t) : cadd(e, t);
-  }
-}
-
-template <bool INV>
-__device__ __forceinline__ void warp_fft256_core(float2 (&v)[8], float2* buf, const float2* __restrict__ tw,
-                                                 int lane) {
-  const int c = lane >> 1, h = lane & 1;
-  warp_fft256_half<INV>(v, h);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int k1 = m + 8 * h;
-    if (k1 > 0) {
-      float2 w = tw[k1 * 16 + c];
-      if (INV) w.y = -w.y;
-      v[m] = cmul(v[m], w);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < 8; ++m) buf[(m + 8 * h) * 17 + c] = v[m];
-  __syncwarp();
-  // pass 2: this lane's row k1 = c (same index), columns 2 i + h
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = buf[c * 17 + 2 * i + h];
-  warp_fft256_half<INV>(v, h);
-  __syncwarp();
-}
-
 }  // namespace elf

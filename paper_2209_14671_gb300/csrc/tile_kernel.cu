@@ -201,100 +201,62 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const int2 org = a.origin[led];
 
   // ---- A: inverse row transforms of this CTA's band rows, pushed into the column owners
-  // one value of band row py at column x into its owner's column buffer (and the neighbours' halos)
-  auto push_a = [&](int x, int py, float2 val) {
-    const int own = x / CW, c = x - own * CW + 1;
-    if constexpr (CS > 1) {
-      const uint32_t e = smem_u32(OC + py * PO + c), m = smem_u32(&mbar[0]);
-      st_async_f2(mapa_u32(e, own), val, mapa_u32(m, own));
-      if (c == CW && own + 1 < CS)  // left halo of the next CTA
-        st_async_f2(mapa_u32(e - 8u * CW, own + 1), val, mapa_u32(m, own + 1));
-      if (c == 1 && own > 0)        // right halo of the previous CTA
-        st_async_f2(mapa_u32(e + 8u * CW, own - 1), val, mapa_u32(m, own - 1));
-    } else {
-      OC[py * PO + c] = val;
-    }
-  };
-  auto first_round_waits = [&]() {  // the twiddles (cp.async group 0) have landed, CTA-wide
-    if (has_meas) {
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    }
-    __syncthreads();
-  };
-  if constexpr (NL == 256) {
-    // a whole warp per band row (warp_fft256): only the warps that own a row work in this stage, so
-    // spreading each row over 32 lanes halves its latency
-    const int c = wl >> 1, hh = wl & 1;
-    for (int base = 0; base < a.rowsA; base += NW) {
-      const int lb = base + warp;
-      const bool act = lb < nrows;
-      float2* row = A1 + (act ? lb : 0) * RP;
-      const int y = a.Blo + b0 + (act ? lb : 0);
-      const int py = FftTeam<NL>::pidx(y);
-      float2 v[8];
-      if (act) {  // crop x pupil at x = c + 16 (2 i + hh); every load issued before the first product
-        const int xs = a.row_xs[y], cnt = a.row_cnt[y];
-        const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
-        const float2* pp = a.pupil + (size_t)y * NL;
-        float2 pv[8];
+  for (int base = 0; base < a.rowsA; base += NTEAM) {
+    const int lb = base + team;
+    const bool act = lb < nrows;
+    float2* row = A1 + (act ? lb : 0) * RP;
+    const int y = a.Blo + b0 + (act ? lb : 0);
+    const int py = FftTeam<NL>::pidx(y);
+    // crop x pupil straight into the registers of the transform's first pass (x = lane + TL j);
+    // every load is issued before the first product
+    constexpr int PL = FftTeam<NL>::P;
+    float2 v[PL];
+    if (act) {
+      const int xs = a.row_xs[y], cnt = a.row_cnt[y];
+      const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
+      const float2* pp = a.pupil + (size_t)y * NL;
+      float2 pv[PL];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int x = c + 16 * (2 * i + hh);
-          const bool in = (unsigned)(x - xs) < (unsigned)cnt;
-          pv[i] = in ? pp[x] : make_float2(0.f, 0.f);
-          v[i] = in ? prow[x] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = cmul(pv[i], v[i]);
+      for (int j = 0; j < PL; ++j) {
+        const int x = lane + TL * j;
+        const bool in = (unsigned)(x - xs) < (unsigned)cnt;
+        pv[j] = in ? pp[x] : make_float2(0.f, 0.f);
+        v[j] = in ? prow[x] : make_float2(0.f, 0.f);
       }
-      if (base == 0) first_round_waits();
-      if (act) warp_fft256_core<true>(v, row, tw, wl);
-      if (base == 0) cluster_wait<CS>();
-      // v[m] = X[c + 16 (m + 8 hh)]: each half-warp stores a contiguous run of the owner's row
-      if (act) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) push_a(c + 16 * (m + 8 * hh), py, v[m]);
-      }
+      for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
     }
-  } else {
-    for (int base = 0; base < a.rowsA; base += NTEAM) {
-      const int lb = base + team;
-      const bool act = lb < nrows;
-      float2* row = A1 + (act ? lb : 0) * RP;
-      const int y = a.Blo + b0 + (act ? lb : 0);
-      const int py = FftTeam<NL>::pidx(y);
-      // crop x pupil straight into the registers of the transform's first pass (x = lane + TL j);
-      // every load is issued before the first product
-      constexpr int PL = FftTeam<NL>::P;
-      float2 v[PL];
-      if (act) {
-        const int xs = a.row_xs[y], cnt = a.row_cnt[y];
-        const float2* prow = a.psi + (size_t)(org.x + y) * a.N + org.y;
-        const float2* pp = a.pupil + (size_t)y * NL;
-        float2 pv[PL];
-#pragma unroll
-        for (int j = 0; j < PL; ++j) {
-          const int x = lane + TL * j;
-          const bool in = (unsigned)(x - xs) < (unsigned)cnt;
-          pv[j] = in ? pp[x] : make_float2(0.f, 0.f);
-          v[j] = in ? prow[x] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
+    if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
+      if (has_meas) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
-      if (base == 0) first_round_waits();
-      team_fft_core<NL, true>(v, row, tw, lane, act);
-      if (base == 0) cluster_wait<CS>();
-      // the transform leaves X[k1 + P k2] in v[m Q + k2] (k1 = lane + Q m): a team's lanes hold
-      // consecutive x, so each store below writes a contiguous run of the owner's row py
-      if (act) {
-        constexpr int Q = FftTeam<NL>::Q;
+      __syncthreads();
+    }
+    team_fft_core<NL, true>(v, row, tw, lane, act);
+    if (base == 0) cluster_wait<CS>();
+    // the transform leaves X[k1 + P k2] in v[m Q + k2] (k1 = lane + Q m): a team's lanes hold
+    // consecutive x, so each store below writes a contiguous run of the owner's row py
+    if (act) {
+      constexpr int Q = FftTeam<NL>::Q;
 #pragma unroll
-        for (int m = 0; m < PL / Q; ++m) {
+      for (int m = 0; m < PL / Q; ++m) {
 #pragma unroll
-          for (int k2 = 0; k2 < Q; ++k2) push_a(lane + Q * m + PL * k2, py, v[m * Q + k2]);
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int x = lane + Q * m + PL * k2;
+          const float2 val = v[m * Q + k2];
+          const int own = x / CW, c = x - own * CW + 1;
+          if constexpr (CS > 1) {
+            const uint32_t e = smem_u32(OC + py * PO + c), m = smem_u32(&mbar[0]);
+            st_async_f2(mapa_u32(e, own), val, mapa_u32(m, own));
+            if (c == CW && own + 1 < CS)  // left halo of the next CTA
+              st_async_f2(mapa_u32(e - 8u * CW, own + 1), val, mapa_u32(m, own + 1));
+            if (c == 1 && own > 0)        // right halo of the previous CTA
+              st_async_f2(mapa_u32(e + 8u * CW, own - 1), val, mapa_u32(m, own - 1));
+          } else {
+            OC[py * PO + c] = val;
+          }
         }
       }
     }
@@ -532,48 +494,27 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
 
   // ---- C: forward row transforms of this CTA's band rows; the support pixels go
   // from the transform's registers straight to G
-  if constexpr (NL == 256) {  // a whole warp per band row, as in stage A
-    const int c = wl >> 1, hh = wl & 1;
-    for (int base = 0; base < a.rowsA; base += NW) {
-      const int lb = base + warp;
-      if (lb >= nrows) continue;  // warp-uniform
-      float2* row = A1 + lb * RP;
-      float2 v[8];
+  for (int base = 0; base < a.rowsA; base += NTEAM) {
+    const int lb = base + team;
+    const bool act = lb < nrows;
+    float2* row = A1 + (act ? lb : 0) * RP;
+    constexpr int PL = FftTeam<NL>::P, Q = FftTeam<NL>::Q;
+    float2 v[PL];
+    if (act) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = row[FftTeam<NL>::pidx(c + 16 * (2 * i + hh))];
-      warp_fft256_core<false>(v, row, tw, wl);
+      for (int j = 0; j < PL; ++j) v[j] = row[lane + (Q + 1) * j];
+    }
+    team_fft_core<NL, false>(v, row, tw, lane, act);
+    if (act) {
       const int ky = a.Blo + b0 + lb;
       const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
       float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int d = c + 16 * (m + 8 * hh) - xs;
-        if ((unsigned)d < (unsigned)cnt) dst[d] = cscale(v[m], a.scale);
-      }
-    }
-  } else {
-    for (int base = 0; base < a.rowsA; base += NTEAM) {
-      const int lb = base + team;
-      const bool act = lb < nrows;
-      float2* row = A1 + (act ? lb : 0) * RP;
-      constexpr int PL = FftTeam<NL>::P, Q = FftTeam<NL>::Q;
-      float2 v[PL];
-      if (act) {
+      for (int m = 0; m < PL / Q; ++m) {
 #pragma unroll
-        for (int j = 0; j < PL; ++j) v[j] = row[lane + (Q + 1) * j];
-      }
-      team_fft_core<NL, false>(v, row, tw, lane, act);
-      if (act) {
-        const int ky = a.Blo + b0 + lb;
-        const int xs = a.row_xs[ky], cnt = a.row_cnt[ky];
-        float2* dst = a.G + (size_t)led * a.S + a.row_off[ky];
-#pragma unroll
-        for (int m = 0; m < PL / Q; ++m) {
-#pragma unroll
-          for (int k2 = 0; k2 < Q; ++k2) {
-            const int d = lane + Q * m + PL * k2 - xs;
-            if ((unsigned)d < (unsigned)cnt) dst[d] = cscale(v[m * Q + k2], a.scale);
-          }
+        for (int k2 = 0; k2 < Q; ++k2) {
+          const int d = lane + Q * m + PL * k2 - xs;
+          if ((unsigned)d < (unsigned)cnt) dst[d] = cscale(v[m * Q + k2], a.scale);
         }
       }
     }
