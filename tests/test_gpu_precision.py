@@ -80,24 +80,36 @@ def test_tensor_core_path_rejects_unsupported_sizes():
     assert ei.value.code == E.ELF_EINVAL
 
 
-def test_fifty_iterations_against_oracle(w3):
-    """50 iterations from the developed state on both tile paths; final relative L2 of Psi
-    and P against the FP64 oracle.  Per-iteration errors of ~1e-7 accumulate along the
-    trajectory (measured: FP32 FFT path 1.4e-4 on Psi, tensor-core path 1.8e-4 on Psi and
-    8e-4 on P after 50 iterations); bounds 3e-4 (FFT) and 2e-3 (tensor cores)."""
+def test_full_run_against_oracle(w3):
+    """The workload's full run (200 iterations, after the 3 of the developed state) on both tile
+    paths; relative L2 of Psi and P against the FP64 oracle, reported every 50 iterations.
+
+    The iteration amplifies small state differences: in the FP64 oracle alone a 1e-7 relative
+    perturbation of Psi and P (FP32 rounding) grows to 1.6e-5 after 50 iterations, so FP32 runs
+    drift from FP64 by more than their per-iteration error. Measured: FFT path Psi 1.4e-4 at 50
+    iterations, 3.4e-5 at 200 (the trajectory converges), P 2.2e-4 at 200; tensor-core path Psi
+    4.6e-5 and P 1.6e-3 at 200. Bounds on the final state: Psi 1e-4 (FFT) and 2e-4 (tensor
+    cores), P 5e-4 and 3e-3."""
     c, st, opt = w3
     I = c["I"].astype(np.float64)
-    ref, _ = O.run(st, I, c["geo"], opt, 50)
+    refs = {}
+    ref = st
+    for it in (50, 100, 150, 200):
+        ref, _ = O.run(ref, I, c["geo"], opt, 50)
+        refs[it] = ref
     errs = {}
     for td in (0, 1):
         with _elf(c, td) as elf:
             elf.set_measurements(c["I"])
             load_state(elf, st)
-            elf.step(50)
-            s = elf.get_state()
-        errs[td] = (rel(s["psi"], ref.psi), rel(s["pupil"], ref.pupil))
-        print(f"tile_dft={td} after 50 iterations: psi {errs[td][0]:.2e} pupil {errs[td][1]:.2e}")
-    assert errs[0][0] < 3e-4 and errs[0][1] < 3e-4 and errs[1][0] < 2e-3 and errs[1][1] < 2e-3
+            for it in (50, 100, 150, 200):
+                elf.step(50)
+                s = elf.get_state()
+                errs[(td, it)] = (rel(s["psi"], refs[it].psi), rel(s["pupil"], refs[it].pupil))
+                print(f"tile_dft={td} after {it} iterations: psi {errs[(td, it)][0]:.2e} "
+                      f"pupil {errs[(td, it)][1]:.2e}")
+    assert errs[(0, 200)][0] < 1e-4 and errs[(0, 200)][1] < 5e-4
+    assert errs[(1, 200)][0] < 2e-4 and errs[(1, 200)][1] < 3e-3
 
 
 @pytest.mark.parametrize("variant", [dict(fidelity=2, g_exponent=0.375), dict(fidelity=3)])
