@@ -185,11 +185,22 @@ __device__ __forceinline__ float2 adabelief_step(float2 g, float2& mu, float& v,
 // Two horizontally adjacent spectrum pixels per thread (16-byte state loads and stores); the
 // threads of a row segment (64 pixels: one warp) walk that segment's list, which holds exactly the
 // LEDs whose support chord crosses it, in ascending order.
+// Block rows run from the centre of the spectrum outwards: the central rows are crossed by the most
+// LEDs and take longest, so they are dispatched first and the short outer rows fill the tail.
 __global__ void __launch_bounds__(256, 5) gather_kernel(const GatherArgs a) {
   const int seg_w = 2 * blockDim.x;
   const int x = blockIdx.x * seg_w + 2 * threadIdx.x;  // first of the thread's two pixels
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int by = blockIdx.y, cb = gridDim.y >> 1;
+  const int rb = (by & 1) ? cb - ((by + 1) >> 1) : cb + (by >> 1);  // covers [0, gridDim.y) for even counts
+  const int y = rb * blockDim.y + threadIdx.y;
   const size_t k = (size_t)y * a.N + x;
+  // the Eq. 19 state is read after the LED loop; ask L2 for it now so the loop covers its latency
+  if (a.mode == 0) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.mu + k));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.v + k));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.delta + k));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psi + k));
+  }
   const int seg = y * a.tiles_x + blockIdx.x;
   const int e0 = a.seg_ptr[seg], e1 = a.seg_ptr[seg + 1];
   // covering LEDs in ascending order; the loads of two entries are issued before their products
