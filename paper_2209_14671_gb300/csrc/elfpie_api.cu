@@ -108,7 +108,8 @@ struct elf_handle_s {
   unsigned char* tc_c[4] = {nullptr, nullptr, nullptr, nullptr};                       // constant images
   float2* tc_Ot = nullptr;
   int* tc_err = nullptr;  // device error flag of the bounded waits (tile exchanges, tensor-core path)
-  float* bc = nullptr;   // Eq. 19 bias corrections of the next iteration
+  float* bc = nullptr;   // Eq. 19 bias corrections, per buffer parity: bc[2p, 2p + 1] for the iteration
+                         // that reads psi_buf[p] (the iteration writes the pair of the other parity)
   double* gp = nullptr;  // (gamma1^(t+1), gamma2^(t+1)) for the next iteration
   std::vector<void*> allocs;
 };
@@ -169,6 +170,10 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
                       float2* psi_out, float2* pupil_out) {
   const bool pupil_path = (mode == 1) || h->opt.learn_pupil;
   const size_t A = (size_t)h->N * h->N;
+  // Eq. 19 bias corrections of this iteration and of the next (double-buffered with Psi)
+  const int par = (psi == h->psi_buf[1]) ? 1 : 0;
+  float* bc_cur = h->bc + 2 * par;
+  float* bc_next = h->bc + 2 * (par ^ 1);
   ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
   // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
   ELF_CK(cudaEventRecord(h->ev_fork, s0));
@@ -205,7 +210,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.v = h->v_p;
   pa.delta = h->delta_p;
   pa.g_out = h->g_p;
-  pa.bc = h->bc;
+  pa.bc = bc_cur;
   pa.N = h->N;
   pa.n = h->n;
   pa.S = h->S;
@@ -320,9 +325,10 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     const bool tc = h->opt.tile_dft != 0, mx = h->mux > 1;
     const double* fid = mx ? h->mux_cost : h->cost_fid;
     const int nfid = tc ? h->K : (mx ? h->n_img * mux_blocks_per_image(h->n) : 0);
+    // in update mode it also closes the iteration (t, running powers, the next bias corrections)
     ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs, h->cost_h,
                               h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out3 : nullptr,
-                              h->aux));
+                              mode == 0 ? bc_next : nullptr, h->gp, h->opt.gamma1, h->opt.gamma2, h->aux));
   }
   ELF_MARK(h->aux, ELF_STAGE_COST, 1);
   ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
@@ -356,7 +362,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.v = h->v_psi;
   ga.delta = h->delta_psi;
   ga.g_out = h->g_psi;
-  ga.bc = h->bc;
+  ga.bc = bc_cur;
   ga.N = h->N;
   ga.n = h->n;
   ga.S = h->S;
@@ -370,9 +376,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_CK(launch_gather(ga, s0));
   ELF_MARK(s0, ELF_STAGE_GATHER, 1);
   if (pupil_path) ELF_CK(cudaStreamWaitEvent(s0, h->ev_pu, 0));  // the pupil chain joins the iteration
-  // the cost reduction has read t before the iteration is closed
+  // the cost reduction (which also closed the iteration) joins it
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_cost, 0));
-  if (mode == 0) ELF_CK(launch_advance(h->t_dev, h->bc, h->gp, h->opt.gamma1, h->opt.gamma2, s0));
   ELF_MARK(s0, ELF_STAGE_ITERATION, 1);
   return ELF_OK;
 }
@@ -455,7 +460,7 @@ int upload_bias(elf_handle h, int t, cudaStream_t s) {
   bc[0] = (float)(1.0 / (1.0 - gp[0]));
   bc[1] = (float)(1.0 / (1.0 - gp[1]));
   ELF_CK(cudaMemcpyAsync(h->gp, gp, sizeof(gp), cudaMemcpyHostToDevice, s));
-  ELF_CK(cudaMemcpyAsync(h->bc, bc, sizeof(bc), cudaMemcpyHostToDevice, s));
+  ELF_CK(cudaMemcpyAsync(h->bc + 2 * h->cur, bc, sizeof(bc), cudaMemcpyHostToDevice, s));
   return ELF_OK;
 }
 
@@ -700,7 +705,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->out3, 3))) return rc;
   if ((rc = dalloc(h, &h->t_dev, 1))) return rc;
   if ((rc = dalloc(h, &h->flag, 1))) return rc;
-  if ((rc = dalloc(h, &h->bc, 2))) return rc;
+  if ((rc = dalloc(h, &h->bc, 4))) return rc;
   if ((rc = dalloc(h, &h->gp, 2))) return rc;
   if (h->opt.tile_dft) {
     const size_t Kz = (size_t)K;
@@ -769,7 +774,7 @@ int init_state_async(elf_handle h) {
   ELF_CK(launch_fill_f(h->v_p, B, 0.f, s));
   ELF_CK(launch_fill_f(h->delta_p, B, (float)(h->opt.s0_pupil * h->opt.s0_pupil), s));
   ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), s));
-  ELF_CK(launch_init_bias(h->bc, h->gp, h->opt.gamma1, h->opt.gamma2, s));
+  ELF_CK(launch_init_bias(h->bc + 2 * h->cur, h->gp, h->opt.gamma1, h->opt.gamma2, s));
   h->have_meas = true;
   return ELF_OK;
 }

@@ -149,9 +149,10 @@ cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s);
 cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
+// bc_next != null (with ring): also t += 1, gp *= gamma and bc_next = the next iteration's corrections.
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
-                               double* ring, const int* t_dev, double* out3, cudaStream_t s);
-cudaError_t launch_advance(int* t_dev, float* bc, double* gp, double g1, double g2, cudaStream_t s);
+                               double* ring, int* t_dev, double* out3, float* bc_next, double* gp, double g1,
+                               double g2, cudaStream_t s);
 cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,

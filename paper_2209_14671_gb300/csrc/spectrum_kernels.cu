@@ -406,10 +406,13 @@ cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s) {
 // ------------------------------------------------------------------ Eq. 8 costs in FP64
 // Sums the partials of Eq. 8's three terms in a fixed order into the cost ring (at
 // iteration t) and/or out3.  It runs beside the gather and pupil kernels, on the stream of
-// the Hessian branch; advance_kernel then closes the iteration.
+// the Hessian branch.  With bc_next it also closes the iteration: t += 1, the running powers
+// gp = (gamma1^(t+1), gamma2^(t+1)) and the next iteration's Eq. 19 bias corrections, written to the
+// other half of the double-buffered pair (the gather and pupil kernels still read this one).
 __global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, int nfid, const float2* fidff, int nff,
                                                            const double* hp, int nh, double* ring,
-                                                           const int* t_dev, double* out3) {
+                                                           int* t_dev, double* out3, float* bc_next, double* gp,
+                                                           double g1, double g2) {
   // per-thread sums over a fixed stride (FP64 partials in FP64, (hi, lo) pairs as pairs),
   // then one block sum of (hi, lo) pairs
   __shared__ float red[2 * 3 * 32];
@@ -448,6 +451,14 @@ __global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, in
       r[0] = a0;
       r[1] = a1;
       r[2] = a2;
+      if (bc_next) {
+        *t_dev = t + 1;
+        const double p1 = gp[0] * g1, p2 = gp[1] * g2;
+        gp[0] = p1;
+        gp[1] = p2;
+        bc_next[0] = (float)(1.0 / (1.0 - p1));
+        bc_next[1] = (float)(1.0 / (1.0 - p2));
+      }
     }
   }
 }
@@ -467,25 +478,9 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
 }
 
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
-                               double* ring, const int* t_dev, double* out3, cudaStream_t s) {
-  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out3);
-  return cudaGetLastError();
-}
-
-// Closes an iteration: t += 1, the running powers gp = (gamma1^(t+1), gamma2^(t+1)) and the bias
-// corrections 1/(1 - gp) of Eq. 19 for the next iteration.
-__global__ void advance_kernel(int* t_dev, float* bc, double* gp, double g1, double g2) {
-  if (threadIdx.x != 0) return;
-  *t_dev += 1;
-  const double p1 = gp[0] * g1, p2 = gp[1] * g2;
-  gp[0] = p1;
-  gp[1] = p2;
-  bc[0] = (float)(1.0 / (1.0 - p1));
-  bc[1] = (float)(1.0 / (1.0 - p2));
-}
-
-cudaError_t launch_advance(int* t_dev, float* bc, double* gp, double g1, double g2, cudaStream_t s) {
-  advance_kernel<<<1, 32, 0, s>>>(t_dev, bc, gp, g1, g2);
+                               double* ring, int* t_dev, double* out3, float* bc_next, double* gp, double g1,
+                               double g2, cudaStream_t s) {
+  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out3, bc_next, gp, g1, g2);
   return cudaGetLastError();
 }
 
