@@ -22,6 +22,7 @@ import math
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -106,8 +107,11 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms.  Reported: the samples read from one
+    period before start() to one period after stop(), i.e. the timed region and the warm-up steps
+    just before it (a short region can fall between two samples)."""
 
+    PERIOD_S = 0.2
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -115,22 +119,44 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
+        self.lines = []  # (host time when read, line)
+        self.t_start = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t0 = time.perf_counter()  # the sampler is live (first line read) before the timed region
+        while not self.lines and time.perf_counter() - t0 < 10.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
+
+    def start(self):
+        self.t_start = time.perf_counter()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        t_end = time.perf_counter()
+        time.sleep(self.PERIOD_S)  # the sample after the region
         self.proc.terminate()
-        out, _ = self.proc.communicate(timeout=10)
+        try:
+            self.proc.wait(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=10)
+        t0 = self.t_start if self.t_start is not None else -float("inf")
+        window = [ln for t, ln in self.lines if t0 - self.PERIOD_S <= t <= t_end + self.PERIOD_S]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in window:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -143,7 +169,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "timed_region_s": round(t_end - t0, 4) if self.t_start is not None else None,
+                "reasons": sorted(reasons)}
 
 
 def oracle_sample_rate(I_host: np.ndarray, w: dict, seconds: float):
@@ -467,6 +494,7 @@ def run_ours(args):
     elf.set_tracing(False)
     kernels_per_step = elf.kernels_per_step()
 
+    clocks = ClockSampler(local)  # live before the warm-up steps, so they and the timed steps are sampled
     for _ in range(args.warmup):
         flush.zero_()
         elf.step(1)
@@ -475,8 +503,8 @@ def run_ours(args):
         torch.distributed.barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
+    clocks.start()
     for i in range(args.steps):
         flush.zero_()                     # L2 flush between timed iterations (outside the events)
         starts[i].record(stream)
