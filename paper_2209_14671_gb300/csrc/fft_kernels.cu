@@ -9,16 +9,19 @@
 
 namespace elf {
 
-// Rows (columns) per CTA: few for long transforms so that a 1024 x 1024 pass
-// launches 512 (256) CTAs, more for short ones; one team of TL lanes each.
+// Rows per CTA: few for long transforms so that a 1024 x 1024 pass launches 256 CTAs, more for
+// short ones; one team of TL lanes each.  Column CTAs have as many teams but twice the columns
+// (each team transforms two), so the row segments they load and store are twice as long (64 bytes
+// for 1024 x 1024) while their registers still fit beside a tile-kernel CTA.
 template <int L>
 struct FftGrid {
   static constexpr int TL = FftTeam<L>::TL;
   static constexpr int PL = FftTeam<L>::PADDED;
   static constexpr int RPC = (128 / TL < L) ? 128 / TL : L;  // rows per CTA (one team each)
-  static constexpr int CPC = (128 / TL < L) ? 128 / TL : L;  // columns per CTA
+  static constexpr int CTEAMS = (128 / TL < L) ? 128 / TL : L;  // teams of a column CTA
+  static constexpr int CPC = (2 * CTEAMS <= L) ? 2 * CTEAMS : CTEAMS;  // columns per CTA
   static constexpr int ROW_THREADS = TL * RPC;
-  static constexpr int COL_THREADS = TL * CPC;
+  static constexpr int COL_THREADS = TL * CTEAMS;
   static constexpr int LD = PL + 1;               // column pitch (odd)
   static constexpr size_t ROW_SMEM = 8 * ((size_t)L + (size_t)RPC * PL);
   static_assert(L % CPC == 0 && L % RPC == 0, "rows and columns per CTA divide L");
@@ -102,7 +105,8 @@ __global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int team = tid / G::TL, lane = tid % G::TL;
-  team_fft<L, INV>(cols + team * LD, tw, lane, true);
+#pragma unroll 1  // one column's values in registers at a time
+  for (int c = team; c < CW; c += G::CTEAMS) team_fft<L, INV>(cols + c * LD, tw, lane, true);  // same count per team
   __syncthreads();
   for (int i = tid; i < CW * L; i += NT) {
     const int y = i / CW, c = i - y * CW;
