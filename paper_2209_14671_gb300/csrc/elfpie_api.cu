@@ -179,8 +179,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ELF_CK(cudaEventRecord(h->ev_fork, s0));
   ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
   ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
-  ELF_CK(cudaMemcpyAsync(h->ot, psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->aux));
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi));  // the first pass reads Psi, writes ot
   HessArgs ha{};
   ha.ot = h->ot;
   ha.q = h->q;

@@ -31,9 +31,10 @@ struct FftGrid {
 // Rows pass: each team transforms one row, reading its pass-1 inputs straight
 // from global memory into registers (coalesced across lanes, all loads in
 // flight at once) and writing its pass-2 outputs straight back; shared memory
-// only carries the transpose between the two passes.
+// only carries the transpose between the two passes.  src may be data (in place) or another
+// array of the same shape (out of place): a row is read whole before it is written.
 template <int L, bool INV>
-__global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(float2* __restrict__ data,
+__global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(const float2* src, float2* data,
                                                                              const float2* __restrict__ twg) {
   using G = FftGrid<L>;
   using T = FftTeam<L>;
@@ -47,10 +48,11 @@ __global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(float
   const int row = blockIdx.x * G::RPC + team;
   const bool act = row < L;
   float2* g = data + (size_t)(act ? row : 0) * L;
+  const float2* gs = src + (size_t)(act ? row : 0) * L;
   float2 v[P];
   if (act) {
 #pragma unroll
-    for (int j = 0; j < P; ++j) v[j] = g[lane + Q * j];
+    for (int j = 0; j < P; ++j) v[j] = gs[lane + Q * j];
   }
   for (int i = tid; i < L; i += NT) tw[i] = twg[i];
   __syncthreads();
@@ -115,9 +117,9 @@ __global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float
 }
 
 template <int L, bool INV>
-static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s) {
+static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src) {
   using G = FftGrid<L>;
-  fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(data, tw);
+  fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(src ? src : data, data, tw);
   fft_cols_kernel<L, INV><<<(L + G::CPC - 1) / G::CPC, G::COL_THREADS, G::COL_SMEM, s>>>(data, tw);
   return cudaGetLastError();
 }
@@ -152,10 +154,10 @@ cudaError_t prepare_fft(int L) {
 #undef ELF_PREP_CASE
 }
 
-cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s) {
+cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s, const float2* src) {
 #define ELF_FFT_CASE(LL)                                                     \
   case LL:                                                                   \
-    return inverse ? fft2_t<LL, true>(data, tw, s) : fft2_t<LL, false>(data, tw, s);
+    return inverse ? fft2_t<LL, true>(data, tw, s, src) : fft2_t<LL, false>(data, tw, s, src);
   switch (L) {
     ELF_FFT_CASE(16)
     ELF_FFT_CASE(32)
