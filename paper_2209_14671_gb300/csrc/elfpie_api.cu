@@ -786,8 +786,7 @@ int handle_set_measurements_async(elf_handle h, const float* I) {
 
 int handle_get_object_async(elf_handle h, float* obj) {
   const size_t A = (size_t)h->N * h->N;
-  ELF_CK(cudaMemcpyAsync(h->ot, h->psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->user));
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi));  // reads Psi, writes ot
   ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
   ELF_CK(cudaMemcpyAsync(obj, h->ot, A * sizeof(float2), cudaMemcpyDefault, h->user));
   return ELF_OK;
@@ -879,8 +878,7 @@ int elf_get_object(elf_handle h, float* obj, int is_device) {
   if (!obj) return set_error(ELF_EINVAL, "null output");
   (void)is_device;
   const size_t A = (size_t)h->N * h->N;
-  ELF_CK(cudaMemcpyAsync(h->ot, h->psi, A * sizeof(float2), cudaMemcpyDeviceToDevice, h->user));
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user));
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi));  // reads Psi, writes ot
   ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
   return copy_out(h, obj, h->ot, A * sizeof(float2));
 }
