@@ -38,9 +38,10 @@ design notes of the repository.  In short:
 * A20 that convolution is circular on the n x n image grid.
 
 Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
-(brute-force DFT, Parseval, adjoint identities, finite differences, affine null
-space of H, closed forms for alpha and the first AdaBelief step, noiseless
-convergence).  The reconstruction-quality numbers of the paper's Tables 2-4 are
+(brute-force DFT, Parseval, adjoint identities, central differences along 32
+seeded directions with a scanned step, affine null space of H, closed forms for
+alpha and the first AdaBelief step, the pupil update of ``iteration`` against a
+hand-summed filter and the closed-form first step, noiseless convergence).  The reconstruction-quality numbers of the paper's Tables 2-4 are
 parity unpinned (their images and comparison codes are not available).
 """
 from __future__ import annotations

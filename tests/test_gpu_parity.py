@@ -8,12 +8,15 @@ Tolerances (relative L2, FP32 CUDA vs FP64 oracle), derived in the design notes:
     (Psi, P); the moments (mu, v, delta) that carry the per-pixel normalised step
     directly: 2e-3 (v) / 5e-3 (delta);
   * workload 0 run for 18 iterations from a developed state: Psi, P, O 1e-4;
-  * the 20-iteration run from the initial state: bounded by the FP32 conditioning
-    of its first phase-Hessian step (Psi 5e-3, see the test's docstring).
+  * the 20-iteration run from the initial state: twice the FP64 oracle's own spread under
+    FP32-sized noise (tests/golden/fp32_spread_w0.json, written by make_fp32_spread.py).
 Sizes: tiny (n=16, one gather tile, ragged LED coverage), single LED, n=32,
 the 64/256/49-LED workload, the 128/512/225-LED workload, and the full-size
 256/1024/225-LED workload in the launch configuration the benchmark times.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -30,6 +33,7 @@ CASES = ["tiny16", "single_led", "nou32", "small32", "w0", "w3", "w1", "wide256"
 TOL_FWD = 1e-5
 TOL_GRAD = 2e-3
 TOL_STATE = 1e-5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -200,11 +204,21 @@ def test_full_run_degraded_workload_matches_oracle():
     assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-3 and e["L_P"] < 1e-3
 
 
+def spread(which, model="fp32", at=None):
+    """The FP64 oracle's own spread under noise of the GPU path's rounding size (largest of the
+    seeded perturbed runs), written by tests/golden/make_fp32_spread.py."""
+    d = json.load(open(os.path.join(GOLDEN, f"fp32_spread_{which}.json")))["spread"][model]
+    return d[str(at) if at is not None else max(d, key=int)]["max"]
+
+
 def test_full_run_from_initial_state_within_fp32_conditioning():
-    """Workload 0 from the initial state.  The initial object is real, so its phase is 0 in
-    FP64 but FP32 rounding noise on the GPU; Eq. 14's omega = H phi / tau amplifies it and
-    the first step diverges (tests/test_oracle_pins.py::test_initial_phase_is_ill_conditioned
-    shows the oracle itself moves Psi by > 1e-3 under 1e-7 noise).  Bounds are set from that."""
+    """Workload 0 from the initial state, where the object is real: its phase is exactly 0 in
+    FP64 and rounding noise in FP32, and Eq. 14's omega = H phi / max(|H phi|, tau) turns that
+    noise into a step (tests/test_oracle_pins.py::test_initial_phase_is_ill_conditioned).  The
+    FP64 oracle itself, with FP32-sized noise injected into its state and its object, ends its
+    20 iterations at a spread of Psi 2.4e-3, P 3.7e-4, L_fid 7.8e-5 from the noiseless run,
+    nearly the same for every noise seed (tests/golden/fp32_spread_w0.json).  The FP32 CUDA
+    path must agree with the FP64 oracle within twice that spread."""
     c = case("w0")
     I = c["I"].astype(np.float64)
     opt = O.Options()
@@ -218,9 +232,11 @@ def test_full_run_from_initial_state_within_fp32_conditioning():
     ce = np.abs(costs - costs_ref) / np.abs(costs_ref)
     e = dict(psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil), L_fid=ce[:, 0].max(),
              L_A=ce[:, 1].max(), L_P=ce[:, 2].max())
-    print("w0 run from t=0", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    sp = spread("w0")
+    print("w0 run from t=0", " ".join(f"{k} {v:.2e} (oracle spread {sp[k]:.2e})" for k, v in e.items()))
     assert ce[0].max() < 1e-5                       # iteration 0 costs: same state, same arithmetic
-    assert e["psi"] < 5e-3 and e["pupil"] < 1e-3 and e["L_fid"] < 1e-3
+    for k in ("psi", "pupil", "L_fid"):
+        assert e[k] <= 2.0 * sp[k], k
 
 
 def test_runs_are_bitwise_reproducible():
