@@ -545,16 +545,24 @@ def init_state(I, geo: Geometry, k_xy, opt: Options) -> State:
         t=0, alpha=float(alpha), beta=float(beta))
 
 
-def iteration(state: State, I, geo: Geometry, opt: Options, want=False):
+def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity=None):
     """One outer iteration of Algorithm 1 from state t to t+1.
 
     Gradients are evaluated at (Psi^t, P^t) (Sec. 3.3-3.4), then Psi and P are
     updated with Eq. 19; P is Gaussian-filtered before its update (A15).
+    ``fidelity``, if given, replaces the call of fidelity_cost_grad (same
+    arguments and results); oracle/parallel.py passes one that splits the LED
+    sum over processes.  It is started before the Hessian branch is evaluated.
     Returns (new_state, costs=(L_fid, L_A, L_Phi) at state t, extras or None).
     """
-    L_fid, g_fid, g_p, tiles = fidelity_cost_grad(state.psi, state.pupil, I, geo, opt,
-                                                  want_tiles=want)
-    L_A, L_P, g_h = hessian_cost_grad(state.psi, state.alpha, state.beta, opt)
+    if fidelity is None:
+        L_fid, g_fid, g_p, tiles = fidelity_cost_grad(state.psi, state.pupil, I, geo, opt,
+                                                      want_tiles=want)
+        L_A, L_P, g_h = hessian_cost_grad(state.psi, state.alpha, state.beta, opt)
+    else:
+        pending = fidelity(state.psi, state.pupil, I, geo, opt, want_tiles=want)
+        L_A, L_P, g_h = hessian_cost_grad(state.psi, state.alpha, state.beta, opt)
+        L_fid, g_fid, g_p, tiles = pending() if callable(pending) else pending
     g_psi = g_fid + g_h
     t = state.t + 1
     s = state.copy()
@@ -572,11 +580,11 @@ def iteration(state: State, I, geo: Geometry, opt: Options, want=False):
     return s, (L_fid, L_A, L_P), extras
 
 
-def run(state: State, I, geo: Geometry, opt: Options, n_iter: int):
+def run(state: State, I, geo: Geometry, opt: Options, n_iter: int, fidelity=None):
     """n_iter iterations; returns (final state, costs [n_iter, 3])."""
     costs = []
     for _ in range(n_iter):
-        state, c, _ = iteration(state, I, geo, opt)
+        state, c, _ = iteration(state, I, geo, opt, fidelity=fidelity)
         costs.append(c)
     return state, np.asarray(costs, dtype=np.float64).reshape(-1, 3)
 
