@@ -91,6 +91,11 @@ typedef struct {
   int tile_dft;      /* tile transforms: 0 = FP32 FFT (default); 1 = tensor-core DFT, BF16 3-term split with
                         FP32 accumulation (not in the paper; n_lowres = 128 with the support band <= 64 only) */
   double g_exponent; /* gamma of the power map (fidelity 2), in (0, 8]; 1 by default (Sec. 6.3) */
+  int tile_path;     /* kernels of the FP32 tile work (same arithmetic): 0 = automatic (default), 1 = one thread-block
+                        cluster per LED, the tile kept on chip; 2 = three kernels per iteration (inverse row
+                        transforms, column transforms + the stencil of Eqs. 5, 12, 11, forward row transforms) that
+                        pass each LED's support band through device memory (2 K nb n complex more, nb = support
+                        rows).  2 needs n_mux = 1 and tile_dft = 0. */
 } elf_options;
 
 /* Full optimiser state of Eq. 19 for Psi and P (Algorithm 1 keeps nothing else).
@@ -125,6 +130,34 @@ int elf_set_measurements(elf_handle h, const float* I, int is_device);
 /* Runs n_iter outer iterations of Algorithm 1 (Eqs. 9-19) asynchronously. */
 int elf_step(elf_handle h, int n_iter);
 
+/* ---- LED sharding of one iteration --------------------------------------------------------
+ * The fidelity gradient is a sum over LEDs (Eq. 9 for Psi, Eq. 18 for P) of terms that each need
+ * only that LED's image and crop (Sec. 3.4), so handles of the same problem in several processes
+ * (or on several GPUs), each holding all the measurements and the same state, can share the LED
+ * work of an iteration.  elf_step(h, 1) is, in order:
+ *   elf_shard_tiles(h, k0, k1)   the tile work (Eqs. 1, 5 or 4, 12, 11 or 10, F_B^H of Eq. 9) of
+ *                                LEDs [k0, k1), plus the LED-free parts that precede the sums: the
+ *                                Hessian branch (Eqs. 6-7, 13-14) and Eq. 19 for P off the support;
+ *   elf_shard_import(h, ...)     for every other block of LEDs, its results from the handle that
+ *                                computed it (elf_shard_export there);
+ *   elf_shard_finish(h)          the sums over all K LEDs in LED order and the rest of the
+ *                                iteration: Eq. 9 + Eq. 19 for Psi, Eq. 18 + the filter + Eq. 19
+ *                                for P, the Eq. 8 costs, t += 1.
+ * The per-LED results are exchanged unsummed and every sum over LEDs runs after the exchange in
+ * LED order, so every handle ends the iteration in a state bitwise equal to elf_step(h, 1), for
+ * any partition of [0, K) into blocks.  Exported block of LEDs [k0, k1) (caller-owned, host or
+ * device, elf_shard_row_floats(h) floats per LED): (k1 - k0) * S complex tile gradients G_n on the
+ * support (LED-major, in the support order of elf_get_support), then (k1 - k0) * C float pairs of
+ * fidelity cost partials (C per LED, the tile kernel's cluster size).  All calls are ordered on
+ * the handle's stream; export into host memory synchronises it.  Sequential FPM (n_mux = 1) with
+ * tile_dft = 0 only (else ELF_EINVAL); elf_step, elf_cost_grad and elf_set_state return
+ * ELF_ESTATE between elf_shard_tiles and elf_shard_finish. */
+int elf_shard_row_floats(elf_handle h);
+int elf_shard_tiles(elf_handle h, int led_begin, int led_end);
+int elf_shard_export(elf_handle h, int led_begin, int led_end, float* dst, int is_device);
+int elf_shard_import(elf_handle h, int led_begin, int led_end, const float* src, int is_device);
+int elf_shard_finish(elf_handle h);
+
 /* Object O = IDFT_N(ifftshift(Psi)) (Algorithm 1 output), [N][N][2] float. */
 int elf_get_object(elf_handle h, float* obj, int is_device);
 /* Current pupil P, [n][n][2] float (zero outside the support). */
@@ -142,9 +175,10 @@ int elf_set_state(elf_handle h, const elf_state* in, int is_device);
 /* Evaluates the cost of Eq. 8 and its Wirtinger gradients dL/d(conj Psi)
  * (Eq. 15 = Eq. 9 + alpha Eq. 13 + beta Eq. 14) and dL/d(conj P) (Eq. 18) at the
  * given (psi [N][N][2], pupil [n][n][2]) with the handle's measurements, alpha and
- * beta, without touching the optimiser state.  costs3 (host) receives
- * (L_fid, L_A, L_Phi) in FP64; g_psi / g_pupil (same layouts) may be NULL. */
-int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs3,
+ * beta, without touching the optimiser state.  costs4 (host, 4 doubles) receives
+ * (L_fid, L_A, L_Phi, L) in FP64, L = L_fid + alpha L_A + beta L_Phi of Eq. 8
+ * summed on the device; g_psi / g_pupil (same layouts) may be NULL. */
+int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs4,
                   float* g_psi, float* g_pupil, int is_device);
 
 /* Forward model of Eq. 1 for data synthesis: I_j = sum over the M LEDs of image j
@@ -188,15 +222,6 @@ int elf_get_stage_spans(elf_handle h, float* spans, int max_stages);
 /* Number of kernel launches in one iteration (kernel nodes of the iteration graph). */
 int elf_graph_kernel_count(elf_handle h);
 
-/* ---- Serving: continuous batching of independent reconstructions ----------
- * (Not in the paper.)  A server admits queued requests in arrival order while a
- * device-memory budget and a slot count allow, runs every admitted request's
- * whole job (measurements upload, initial state, n_iter iterations, object) on
- * its own stream so that jobs overlap on the device, and retires finished jobs
- * without blocking.  Handles are pooled per (problem, options) and reused; idle
- * pooled handles are freed, least recently used first, when a new shape needs
- * room.  A request's result is bitwise the same as a lone run of the same job. */
-typedef struct elf_server_s* elf_server;
 /* ---- evaluation of Sec. 4.1 (Eqs. 20-22); device pointers, the call synchronises ---- */
 
 /* Degradation parameters of Eqs. 2 and 20. */
@@ -233,6 +258,16 @@ int elf_lsnr(const float* rec, const float* truth, long long count, void* cuda_s
  * is not observable from intensities).  Writes out2[0] (amplitude), out2[1] (phase) on the host. */
 int elf_object_quality(elf_handle h, const float* obj_true, double* out2);
 
+/* ---- Serving: continuous batching of independent reconstructions ----------
+ * (Not in the paper.)  A server admits queued requests in arrival order while a
+ * device-memory budget and a slot count allow, runs every admitted request's
+ * whole job (measurements upload, initial state, n_iter iterations, object) on
+ * its own stream so that jobs overlap on the device, and retires finished jobs
+ * without blocking.  Handles are pooled per (problem, options) and reused; idle
+ * pooled handles are freed, least recently used first, when a new shape needs
+ * room.  A request's result is bitwise the same as a lone run of the same job. */
+typedef struct elf_server_s* elf_server;
+
 /* budget_bytes: device memory the server may hold; max_active: concurrent jobs. */
 int elf_server_create(size_t budget_bytes, int max_active, elf_server* out);
 /* Queues a request.  I [K][n][n] float (host; pinned memory makes the upload
@@ -267,12 +302,22 @@ void elf_server_destroy(elf_server s);
  * A problem needing more partials than that (n_led * ceil((n_lowres - 2) / 16))
  * is rejected with ELF_EINVAL before any GPU work.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture.  All calls share
- * the array; each call overwrites every partial it reads, so nothing needs
- * clearing, but calls that overlap on the GPU race. */
+ * current and keeps it, so make that first call before any stream capture; the
+ * kept address dies with the device's primary context, so do not call this
+ * again on a device after cudaDeviceReset.  All calls share the array; each call
+ * overwrites every partial it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU race. */
 #define ELF_NOALLOC_WEIGHT_MAX_PARTIALS 16384
 int elf_estimate_weights_noalloc(const float* I, int n_led, int n_lowres, int fidelity, double* weights,
                                  void* cuda_stream);
+
+/* ---- Measured FP32 peak (for the roofline of the FP32-bound tile kernel; not in the paper) ----
+ * Runs an FMA-throughput kernel on the current device: 8 blocks of 256 threads per SM, each
+ * thread iters x 8 independent FMAs; repeats timed launches (CUDA events on cuda_stream,
+ * which may be NULL) after one warm-up launch.  Writes the best launch's throughput in
+ * TFLOP/s (2 FLOP per FMA) to *tflops and its duration to *best_ms (may be NULL).
+ * Synchronises the stream.  Allocates no device memory; changes no device setting. */
+int elf_measure_fp32_peak(int iters, int repeats, void* cuda_stream, double* tflops, double* best_ms);
 
 void elf_destroy(elf_handle h);
 const char* elf_strerror(int code);

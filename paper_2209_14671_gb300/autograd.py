@@ -1,7 +1,8 @@
 """Differentiation form: the Elfpie cost of Eq. 8 as a torch.autograd.Function.
 
 forward(psi, pupil) returns L = L_fid + alpha L_A + beta L_Phi (Eq. 8) for the
-handle's measurements, reduced in FP64 on the GPU; the same library call
+handle's measurements, reduced and weighted in FP64 on the GPU by the library
+(elf_cost_grad returns the total beside its three terms); the same call
 (elf_cost_grad) produces the closed-form Wirtinger gradients dL/d(conj Psi)
 (Eq. 15 = Eq. 9 + alpha Eq. 13 + beta Eq. 14) and dL/d(conj P) (Eq. 18) in the
 same pass, and backward returns them scaled.  PyTorch's convention for a real
@@ -30,11 +31,9 @@ class ElfCostFunction(torch.autograd.Function):
         g_psi = torch.empty_like(psi_c)
         g_pup = torch.empty_like(pup_c)
         costs, _, _ = elf.cost_grad(psi_c, pup_c, g_psi, g_pup)
-        alpha, beta = elf.get_weights()
-        total = float(costs[0] + alpha * costs[1] + beta * costs[2])
         ctx.save_for_backward(g_psi, g_pup)
         ctx.costs = costs
-        return torch.tensor(total, dtype=torch.float64, device=psi.device)
+        return torch.tensor(costs[3], dtype=torch.float64, device=psi.device)  # Eq. 8's total, from the library
 
     @staticmethod
     @torch.autograd.function.once_differentiable

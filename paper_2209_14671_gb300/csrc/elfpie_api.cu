@@ -60,6 +60,10 @@ struct elf_handle_s {
               ev_pu = nullptr;
   bool have_meas = false;
   bool tracing = false;
+  bool shard_open = false;  // elf_shard_tiles ran; elf_shard_finish has not
+  bool split = false;       // the tile work runs as the three split kernels (tile_split.cu)
+  float2 *band_in = nullptr, *band_out = nullptr;  // their K x nb x n support bands
+  int shard_k0 = 0, shard_k1 = 0;
   int graph_kernels = 0;
   cudaEvent_t ev_stage[2 * ELF_NSTAGES] = {};
   cudaGraphExec_t graph[2] = {};  // iteration from psi_buf[p] into psi_buf[p ^ 1]
@@ -100,7 +104,7 @@ struct elf_handle_s {
   float2 *psi_eval = nullptr, *pupil_eval = nullptr, *g_psi = nullptr, *g_p = nullptr, *pupil_unit = nullptr;
   float2* cost_ff = nullptr;  // per-warp (hi, lo) fidelity cost partials of the tile kernel
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
-         *out3 = nullptr;
+         *out4 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
   size_t device_bytes = 0;  // sum of this handle's device allocations
   // tensor-core tile path (tile_dft = 1)
@@ -163,38 +167,25 @@ int mark(elf_handle h, cudaStream_t s, int stage, int end) {
     if (int rc_ = mark(h, (s), (stage), (end))) return rc_; \
   } while (0)
 
+// Parts of one iteration (enqueue_iteration): the front part forks the Hessian branch and the
+// off-support pupil update onto the auxiliary stream and runs the tile kernel for LEDs
+// [led_begin, led_end) on s0; the back part (every LED's tile results present) runs the Eq. 8 cost
+// reduction, the pupil chain and the gather, and joins the streams into s0.
+enum { kPartFront = 1, kPartBack = 2, kPartAll = 3 };
+
 // One outer iteration of Algorithm 1 (mode 0) or a gradient evaluation (mode 1).
 // In mode 0 the gather writes Psi^(t+1) into psi_out (not psi, which the pupil chain still reads)
 // and the pupil update writes P^(t+1) into pupil_out (not pupil, which the gather still reads).
+// parts selects the front and / or back part; the tile kernel covers LEDs [led_begin, led_end).
 int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi, const float2* pupil,
-                      float2* psi_out, float2* pupil_out) {
+                      float2* psi_out, float2* pupil_out, int parts = kPartAll, int led_begin = 0, int led_end = -1) {
   const bool pupil_path = (mode == 1) || h->opt.learn_pupil;
   const size_t A = (size_t)h->N * h->N;
+  if (led_end < 0) led_end = h->K;
   // Eq. 19 bias corrections of this iteration and of the next (double-buffered with Psi)
   const int par = (psi == h->psi_buf[1]) ? 1 : 0;
   float* bc_cur = h->bc + 2 * par;
   float* bc_next = h->bc + 2 * (par ^ 1);
-  ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
-  // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
-  ELF_CK(cudaEventRecord(h->ev_fork, s0));
-  ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-  ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi));  // the first pass reads Psi, writes ot
-  HessArgs ha{};
-  ha.ot = h->ot;
-  ha.q = h->q;
-  ha.costpart = h->cost_h;
-  ha.weights = h->weights;
-  ha.N = h->N;
-  ha.invA = (float)(1.0 / (double)A);
-  ha.tau = (float)h->opt.tau_h;
-  ha.eta = (float)h->opt.eta_h;
-  ha.iso = h->opt.omega_iso;
-  ELF_CK(launch_hessian(ha, h->aux));
-  ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux));
-  ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
-  ELF_CK(cudaEventRecord(h->ev_join, h->aux));
-
   PupilArgs pa{};
   pa.G = h->G;
   pa.psi = psi;
@@ -223,95 +214,123 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.eta = (float)h->opt.eta_opt;
   pa.mode = mode;
   pa.done = h->pdone;
-  // Eq. 19 off the support (gradient 0) needs nothing from the tile kernel: it runs on the auxiliary
-  // stream after the Hessian branch, on the SMs the tile clusters leave free
-  if (pupil_path) {
-    ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 0);
-    ELF_CK(launch_pupil_offsupport(pa, h->aux));
-    ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 1);
-  }
+  if (parts & kPartFront) {
+    ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
+    // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
+    ELF_CK(cudaEventRecord(h->ev_fork, s0));
+    ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
+    ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi));  // the first pass reads Psi, writes ot
+    HessArgs ha{};
+    ha.ot = h->ot;
+    ha.q = h->q;
+    ha.costpart = h->cost_h;
+    ha.weights = h->weights;
+    ha.N = h->N;
+    ha.invA = (float)(1.0 / (double)A);
+    ha.tau = (float)h->opt.tau_h;
+    ha.eta = (float)h->opt.eta_h;
+    ha.iso = h->opt.omega_iso;
+    ELF_CK(launch_hessian(ha, h->aux));
+    ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux));
+    ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
+    ELF_CK(cudaEventRecord(h->ev_join, h->aux));
 
-  // tile path: Eqs. 1, 5 (4), 12, 11 (10) and F_B^H of Eq. 9
-  TileArgs ta{};
-  ta.psi = psi;
-  ta.pupil = pupil;
-  ta.meas = h->opt.fidelity >= 1 ? h->Ig : h->I;
-  ta.origin = h->origin;
-  ta.row_xs = h->row_xs;
-  ta.row_cnt = h->row_cnt;
-  ta.row_off = h->row_off;
-  ta.tw = h->tw_n;
-  ta.G = h->G;
-  ta.cost_ff = h->cost_ff;
-  ta.err = h->tc_err;
-  ta.I_out = nullptr;
-  ta.N = h->N;
-  ta.K = h->K;
-  ta.S = h->S;
-  ta.Blo = h->Blo;
-  ta.nb = h->nb;
-  ta.rowsA = h->rowsA;
-  ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
-  ta.tau = (float)h->opt.tau_fid;
-  ta.eta = (float)h->opt.eta_h;
-  ta.gexp = (float)h->opt.g_exponent;
-  ta.fidelity = h->opt.fidelity;
-  ta.iso = h->opt.omega_iso;
-  ta.mode = 0;
-  ta.mux = h->mux;
-  ELF_MARK(s0, ELF_STAGE_TILE, 0);
-  if (h->opt.tile_dft) {
-    TcArgs tc{};
-    tc.psi = psi;
-    tc.pupil = pupil;
-    tc.origin = h->origin;
-    tc.row_xs = h->row_xs;
-    tc.row_cnt = h->row_cnt;
-    tc.row_off = h->row_off;
-    tc.meas = ta.meas;
-    tc.cA1 = h->tc_c[0];
-    tc.cB2 = h->tc_c[1];
-    tc.cA3 = h->tc_c[2];
-    tc.cB4 = h->tc_c[3];
-    tc.iX = h->tc_iX;
-    tc.iY = h->tc_iY;
-    tc.iW = h->tc_iW;
-    tc.iZ = h->tc_iZ;
-    tc.Ot = h->tc_Ot;
-    tc.G = h->G;
-    tc.costpart = h->cost_fid;
-    tc.err = h->tc_err;
-    tc.n = h->n;
-    tc.N = h->N;
-    tc.K = h->K;
-    tc.S = h->S;
-    tc.Blo = h->Blo;
-    tc.nb = h->nb;
-    tc.scale = ta.scale;
-    tc.tau = ta.tau;
-    tc.eta = ta.eta;
-    tc.gexp = ta.gexp;
-    tc.fidelity = ta.fidelity;
-    tc.iso = ta.iso;
-    ELF_CK(launch_tc_tile(tc, s0));
-  } else if (h->mux > 1) {
-    // multiplexed images: |o|^2 of every LED, per-image residual / normaliser / factor f, then
-    // W = o f per LED (mux_kernels.cu)
-    TileArgs t1 = ta;
-    t1.mode = 1;
-    t1.I_out = h->Imod;
-    ELF_CK(launch_tile(t1, h->n, s0));
-    ELF_CK(launch_mux_resid(h->Imod, ta.meas, h->mux_r, h->mux_f, h->n_img, h->mux, h->n, h->opt.fidelity, ta.gexp,
-                            ta.eta, s0));
-    ELF_CK(launch_mux_omega(h->mux_r, h->mux_f, h->mux_cost, h->n_img, h->n, ta.tau, ta.iso, s0));
-    TileArgs t2 = ta;
-    t2.mode = 2;
-    t2.meas = h->mux_f;
-    ELF_CK(launch_tile(t2, h->n, s0));
-  } else {
-    ELF_CK(launch_tile(ta, h->n, s0));
-  }
-  ELF_MARK(s0, ELF_STAGE_TILE, 1);
+    // Eq. 19 off the support (gradient 0) needs nothing from the tile kernel: it runs on the auxiliary
+    // stream after the Hessian branch, on the SMs the tile clusters leave free
+    if (pupil_path) {
+      ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 0);
+      ELF_CK(launch_pupil_offsupport(pa, h->aux));
+      ELF_MARK(h->aux, ELF_STAGE_PUPIL_UPDATE, 1);
+    }
+
+    // tile path: Eqs. 1, 5 (4), 12, 11 (10) and F_B^H of Eq. 9
+    TileArgs ta{};
+    ta.psi = psi;
+    ta.pupil = pupil;
+    ta.meas = h->opt.fidelity >= 1 ? h->Ig : h->I;
+    ta.origin = h->origin;
+    ta.row_xs = h->row_xs;
+    ta.row_cnt = h->row_cnt;
+    ta.row_off = h->row_off;
+    ta.tw = h->tw_n;
+    ta.G = h->G;
+    ta.cost_ff = h->cost_ff;
+    ta.err = h->tc_err;
+    ta.I_out = nullptr;
+    ta.N = h->N;
+    ta.K = h->K;
+    ta.S = h->S;
+    ta.Blo = h->Blo;
+    ta.nb = h->nb;
+    ta.rowsA = h->rowsA;
+    ta.scale = (float)(1.0 / ((double)h->u * h->u * (double)h->n * h->n));
+    ta.tau = (float)h->opt.tau_fid;
+    ta.eta = (float)h->opt.eta_h;
+    ta.gexp = (float)h->opt.g_exponent;
+    ta.fidelity = h->opt.fidelity;
+    ta.iso = h->opt.omega_iso;
+    ta.mode = 0;
+    ta.mux = h->mux;
+    ta.led0 = led_begin;
+    ta.nled = led_end - led_begin;
+    ELF_MARK(s0, ELF_STAGE_TILE, 0);
+    if (h->opt.tile_dft) {
+      TcArgs tc{};
+      tc.psi = psi;
+      tc.pupil = pupil;
+      tc.origin = h->origin;
+      tc.row_xs = h->row_xs;
+      tc.row_cnt = h->row_cnt;
+      tc.row_off = h->row_off;
+      tc.meas = ta.meas;
+      tc.cA1 = h->tc_c[0];
+      tc.cB2 = h->tc_c[1];
+      tc.cA3 = h->tc_c[2];
+      tc.cB4 = h->tc_c[3];
+      tc.iX = h->tc_iX;
+      tc.iY = h->tc_iY;
+      tc.iW = h->tc_iW;
+      tc.iZ = h->tc_iZ;
+      tc.Ot = h->tc_Ot;
+      tc.G = h->G;
+      tc.costpart = h->cost_fid;
+      tc.err = h->tc_err;
+      tc.n = h->n;
+      tc.N = h->N;
+      tc.K = h->K;
+      tc.S = h->S;
+      tc.Blo = h->Blo;
+      tc.nb = h->nb;
+      tc.scale = ta.scale;
+      tc.tau = ta.tau;
+      tc.eta = ta.eta;
+      tc.gexp = ta.gexp;
+      tc.fidelity = ta.fidelity;
+      tc.iso = ta.iso;
+      ELF_CK(launch_tc_tile(tc, s0));
+    } else if (h->mux > 1) {
+      // multiplexed images: |o|^2 of every LED, per-image residual / normaliser / factor f, then
+      // W = o f per LED (mux_kernels.cu)
+      TileArgs t1 = ta;
+      t1.mode = 1;
+      t1.I_out = h->Imod;
+      ELF_CK(launch_tile(t1, h->n, s0));
+      ELF_CK(launch_mux_resid(h->Imod, ta.meas, h->mux_r, h->mux_f, h->n_img, h->mux, h->n, h->opt.fidelity, ta.gexp,
+                              ta.eta, s0));
+      ELF_CK(launch_mux_omega(h->mux_r, h->mux_f, h->mux_cost, h->n_img, h->n, ta.tau, ta.iso, s0));
+      TileArgs t2 = ta;
+      t2.mode = 2;
+      t2.meas = h->mux_f;
+      ELF_CK(launch_tile(t2, h->n, s0));
+    } else if (ta.nled > 0 && h->split) {
+      ELF_CK(launch_tile_split(ta, h->n, h->band_in, h->band_out, s0));
+    } else if (ta.nled > 0) {
+      ELF_CK(launch_tile(ta, h->n, s0));
+    }
+    ELF_MARK(s0, ELF_STAGE_TILE, 1);
+  }  // front part
+  if (!(parts & kPartBack)) return ELF_OK;
 
   // Eq. 8 costs on the auxiliary stream once the Hessian partials (same stream) and the tile
   // kernel's partials exist, beside the gather and pupil kernels below
@@ -326,8 +345,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     const int nfid = tc ? h->K : (mx ? h->n_img * mux_blocks_per_image(h->n) : 0);
     // in update mode it also closes the iteration (t, running powers, the next bias corrections)
     ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs, h->cost_h,
-                              h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out3 : nullptr,
-                              mode == 0 ? bc_next : nullptr, h->gp, h->opt.gamma1, h->opt.gamma2, h->aux));
+                              h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out4 : nullptr,
+                              h->weights, mode == 0 ? bc_next : nullptr, h->gp, h->opt.gamma1, h->opt.gamma2, h->aux));
   }
   ELF_MARK(h->aux, ELF_STAGE_COST, 1);
   ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
@@ -496,6 +515,7 @@ int elf_default_options(elf_options* o) {
   o->tau_h = 1e-4;
   o->tile_dft = 0;
   o->g_exponent = 1.0;
+  o->tile_path = 0;
   return ELF_OK;
 }
 
@@ -536,11 +556,15 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if (!(op.gamma1 >= 0 && op.gamma1 < 1 && op.gamma2 >= 0 && op.gamma2 < 1 && op.tau_fid >= 0 && op.tau_h >= 0 &&
         op.eta_opt >= 0 && op.eta_h >= 0 && op.s0_psi >= 0 && op.s0_pupil >= 0 && std::isfinite(op.alpha) &&
         std::isfinite(op.beta) && op.fidelity >= 0 && op.fidelity <= 3 && (op.tile_dft == 0 || op.tile_dft == 1) &&
-        (op.fidelity != 2 || (std::isfinite(op.g_exponent) && op.g_exponent > 0 && op.g_exponent <= 8))))
+        (op.fidelity != 2 || (std::isfinite(op.g_exponent) && op.g_exponent > 0 && op.g_exponent <= 8)) &&
+        op.tile_path >= 0 && op.tile_path <= 2))
     return set_error(ELF_EINVAL, "invalid options");
   const int M = p->n_mux <= 0 ? 1 : p->n_mux;
   if (M > K || K % M != 0) return set_error(ELF_EINVAL, "n_led must be a positive multiple of n_mux");
   if (M > 1 && op.tile_dft) return set_error(ELF_EINVAL, "multiplexed images (n_mux > 1) need tile_dft = 0");
+  if (op.tile_path == 2 && (M > 1 || op.tile_dft))
+    return set_error(ELF_EINVAL, "tile_path = 2 needs n_mux = 1 and tile_dft = 0");
+  h->split = tile_split_selected(n, M, op.tile_dft, op.tile_path);
   h->mux = M;
   h->n_img = K / M;
   h->n = n;
@@ -701,7 +725,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->ring, (size_t)3 * kCostRing))) return rc;
   if ((rc = dalloc(h, &h->weights, 2))) return rc;
   if ((rc = dalloc(h, &h->alpha_part, (size_t)alpha_blocks(K, n)))) return rc;
-  if ((rc = dalloc(h, &h->out3, 3))) return rc;
+  if ((rc = dalloc(h, &h->out4, 4))) return rc;
   if ((rc = dalloc(h, &h->t_dev, 1))) return rc;
   if ((rc = dalloc(h, &h->flag, 1))) return rc;
   if ((rc = dalloc(h, &h->bc, 4))) return rc;
@@ -721,6 +745,11 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
     ELF_CK(prepare_tc());
   }
   ELF_CK(prepare_tile(n, h->rowsA));
+  if (h->split) {
+    if ((rc = dalloc(h, &h->band_in, (size_t)K * h->nb * n))) return rc;
+    if ((rc = dalloc(h, &h->band_out, (size_t)K * h->nb * n))) return rc;
+    ELF_CK(prepare_tile_split(n));
+  }
   ELF_CK(prepare_fft(n));
   ELF_CK(prepare_fft(N));
   ELF_CK(launch_support_pupil(h->pupil_unit, h->sidx_map, n, h->user));
@@ -837,6 +866,7 @@ extern "C" int elf_set_measurements(elf_handle h, const float* I, int is_device)
     return set_error(ELF_EINVAL, "measurements contain NaN or Inf");
   }
   if (int rc = init_state_async(h)) return rc;
+  h->shard_open = false;
   ELF_CK(cudaStreamSynchronize(s));
   return ELF_OK;
 }
@@ -846,6 +876,7 @@ extern "C" {
 int elf_step(elf_handle h, int n_iter) {
   if (int rc = check(h)) return rc;
   if (!h->have_meas) return set_error(ELF_ESTATE, "elf_step before elf_set_measurements");
+  if (h->shard_open) return set_error(ELF_ESTATE, "elf_step inside a sharded iteration (elf_shard_finish first)");
   if (n_iter < 0) return set_error(ELF_EINVAL, "negative n_iter");
   if (int rc = build_graph(h)) return rc;
   for (; !h->tracing && n_iter >= kGraphIters; n_iter -= kGraphIters)
@@ -856,6 +887,71 @@ int elf_step(elf_handle h, int n_iter) {
     h->psi = h->psi_buf[h->cur];
     if (h->opt.learn_pupil) h->pupil = h->pupil_buf[h->cur];
   }
+  return ELF_OK;
+}
+
+// ---- LED sharding: one iteration split around an exchange of the per-LED tile results
+static int shard_check(elf_handle h, int k0, int k1) {
+  if (int rc = check(h)) return rc;
+  if (h->mux > 1 || h->opt.tile_dft) return set_error(ELF_EINVAL, "sharding needs n_mux = 1 and tile_dft = 0");
+  if (k0 < 0 || k1 < k0 || k1 > h->K) return set_error(ELF_EINVAL, "LED range outside [0, n_led]");
+  return ELF_OK;
+}
+
+int elf_shard_row_floats(elf_handle h) {
+  if (int rc = check(h)) return rc;
+  return 2 * (h->S + h->cs);
+}
+
+int elf_shard_tiles(elf_handle h, int led_begin, int led_end) {
+  if (int rc = shard_check(h, led_begin, led_end)) return rc;
+  if (!h->have_meas) return set_error(ELF_ESTATE, "elf_shard_tiles before elf_set_measurements");
+  if (h->shard_open) return set_error(ELF_ESTATE, "elf_shard_tiles twice without elf_shard_finish");
+  const int q = h->cur;
+  const bool lp = h->opt.learn_pupil != 0;
+  if (int rc = enqueue_iteration(h, 0, h->user, h->psi_buf[q], h->pupil_buf[lp ? q : 0], h->psi_buf[q ^ 1],
+                                 lp ? h->pupil_buf[q ^ 1] : nullptr, kPartFront, led_begin, led_end))
+    return rc;
+  h->shard_open = true;
+  h->shard_k0 = led_begin;
+  h->shard_k1 = led_end;
+  return ELF_OK;
+}
+
+int elf_shard_export(elf_handle h, int led_begin, int led_end, float* dst, int is_device) {
+  if (int rc = shard_check(h, led_begin, led_end)) return rc;
+  if (!dst) return set_error(ELF_EINVAL, "null destination");
+  const size_t nl = (size_t)(led_end - led_begin), gb = nl * h->S * sizeof(float2);
+  ELF_CK(cudaMemcpyAsync(dst, h->G + (size_t)led_begin * h->S, gb, cudaMemcpyDefault, h->user));
+  ELF_CK(cudaMemcpyAsync(reinterpret_cast<char*>(dst) + gb, h->cost_ff + (size_t)led_begin * h->cs,
+                         nl * h->cs * sizeof(float2), cudaMemcpyDefault, h->user));
+  if (!is_device) ELF_CK(cudaStreamSynchronize(h->user));
+  return ELF_OK;
+}
+
+int elf_shard_import(elf_handle h, int led_begin, int led_end, const float* src, int is_device) {
+  if (int rc = shard_check(h, led_begin, led_end)) return rc;
+  if (!src) return set_error(ELF_EINVAL, "null source");
+  (void)is_device;
+  const size_t nl = (size_t)(led_end - led_begin), gb = nl * h->S * sizeof(float2);
+  ELF_CK(cudaMemcpyAsync(h->G + (size_t)led_begin * h->S, src, gb, cudaMemcpyDefault, h->user));
+  ELF_CK(cudaMemcpyAsync(h->cost_ff + (size_t)led_begin * h->cs, reinterpret_cast<const char*>(src) + gb,
+                         nl * h->cs * sizeof(float2), cudaMemcpyDefault, h->user));
+  return ELF_OK;
+}
+
+int elf_shard_finish(elf_handle h) {
+  if (int rc = check(h)) return rc;
+  if (!h->shard_open) return set_error(ELF_ESTATE, "elf_shard_finish without elf_shard_tiles");
+  const int q = h->cur;
+  const bool lp = h->opt.learn_pupil != 0;
+  h->shard_open = false;
+  if (int rc = enqueue_iteration(h, 0, h->user, h->psi_buf[q], h->pupil_buf[lp ? q : 0], h->psi_buf[q ^ 1],
+                                 lp ? h->pupil_buf[q ^ 1] : nullptr, kPartBack))
+    return rc;
+  h->cur ^= 1;  // Psi^(t+1) and P^(t+1) are in the other buffers, as after elf_step
+  h->psi = h->psi_buf[h->cur];
+  if (lp) h->pupil = h->pupil_buf[h->cur];
   return ELF_OK;
 }
 
@@ -943,6 +1039,7 @@ int elf_set_state(elf_handle h, const elf_state* st, int is_device) {
   if (st->t < 0 || !std::isfinite(st->alpha) || !std::isfinite(st->beta) || st->alpha < 0 || st->beta < 0)
     return set_error(ELF_EINVAL, "invalid t, alpha or beta");
   if (!h->have_meas) return set_error(ELF_ESTATE, "elf_set_state before elf_set_measurements");
+  if (h->shard_open) return set_error(ELF_ESTATE, "elf_set_state inside a sharded iteration");
   (void)is_device;
   const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
   cudaStream_t s = h->user;
@@ -963,11 +1060,12 @@ int elf_set_state(elf_handle h, const elf_state* st, int is_device) {
   return ELF_OK;
 }
 
-int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs3, float* g_psi, float* g_pupil,
+int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* costs4, float* g_psi, float* g_pupil,
                   int is_device) {
   if (int rc = check(h)) return rc;
   if (!psi || !pupil) return set_error(ELF_EINVAL, "null psi or pupil");
   if (!h->have_meas) return set_error(ELF_ESTATE, "elf_cost_grad before elf_set_measurements");
+  if (h->shard_open) return set_error(ELF_ESTATE, "elf_cost_grad inside a sharded iteration");
   (void)is_device;
   const size_t A = (size_t)h->N * h->N, B = (size_t)h->n * h->n;
   cudaStream_t s = h->user;
@@ -976,15 +1074,15 @@ int elf_cost_grad(elf_handle h, const float* psi, const float* pupil, double* co
   if (int rc = enqueue_iteration(h, 1, s, h->psi_eval, h->pupil_eval, nullptr, nullptr)) return rc;
   if (g_psi) ELF_CK(cudaMemcpyAsync(g_psi, h->g_psi, A * 8, cudaMemcpyDefault, s));
   if (g_pupil) ELF_CK(cudaMemcpyAsync(g_pupil, h->g_p, B * 8, cudaMemcpyDefault, s));
-  double c[3];
-  ELF_CK(cudaMemcpyAsync(c, h->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double c[4];
+  ELF_CK(cudaMemcpyAsync(c, h->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ELF_CK(cudaStreamSynchronize(s));
   if (h->tc_err) {
     int bad = 0;
     ELF_CK(cudaMemcpy(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (bad) return set_error(ELF_ETIMEOUT, "a bounded device wait ran out; results are invalid");
   }
-  if (costs3) std::memcpy(costs3, c, sizeof(c));
+  if (costs4) std::memcpy(costs4, c, sizeof(c));
   for (double v : c)
     if (!std::isfinite(v)) return set_error(ELF_ENUMERIC, "non-finite cost");
   return ELF_OK;

@@ -35,12 +35,20 @@ struct TileArgs {
   int mode;               // 0 = gradient, 1 = simulate |o|^2, 2 = gradient of multiplexed images:
                           // meas holds the per-image factor f (mux_kernels.cu), W = o f
   int mux;                // M: LEDs per image; LED k reads image k / M in mode 2
+  int led0, nled;         // LEDs [led0, led0 + nled) (nled = 0: all K from LED 0)
 };
 int tile_cluster_size(int n);
 int tile_warps(int n);                        // warps per CTA of the tile kernel
 size_t tile_smem_bytes(int n, int cs, int rowsA);
 cudaError_t prepare_tile(int n, int rowsA);   // sets kernel attributes; call outside capture
 cudaError_t launch_tile(const TileArgs& a, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------- split tile path (tile_split.cu)
+// The same tile work as three kernels (inverse rows, columns + stencil, forward rows) with the support
+// band of each LED in device memory: band_in / band_out hold K x nb x n complex each.  Gradient mode only.
+bool tile_split_selected(int n, int mux, int tile_dft, int tile_path);
+cudaError_t prepare_tile_split(int n);        // sets kernel attributes; call outside capture
+cudaError_t launch_tile_split(const TileArgs& a, int n, float2* band_in, float2* band_out, cudaStream_t s);
 
 // ---------------------------------------------------------------- multiplexed images (mux_kernels.cu)
 int mux_blocks_per_image(int n);  // cost partials per image of mux_omega
@@ -151,10 +159,11 @@ cudaError_t launch_pupil_partial(const PupilArgs& a, cudaStream_t s);
 cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions / setup
+// out4 != null: (L_fid, L_A, L_Phi, L) with L = L_fid + weights[0] L_A + weights[1] L_Phi (Eq. 8).
 // bc_next != null (with ring): also t += 1, gp *= gamma and bc_next = the next iteration's corrections.
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
-                               double* ring, int* t_dev, double* out3, float* bc_next, double* gp, double g1,
-                               double g2, cudaStream_t s);
+                               double* ring, int* t_dev, double* out4, const double* weights, float* bc_next,
+                               double* gp, double g1, double g2, cudaStream_t s);
 cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,

@@ -12,7 +12,10 @@
 // loads this library keeps until the process exits.  Host code cannot use the
 // array's name as a device address (in host code it names a host-side stand-in),
 // so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current, and caches it.
+// cudaGetSymbolAddress while that device is current, and caches it.  The cached
+// address belongs to the device's primary context: after cudaDeviceReset on that
+// device the module is loaded again elsewhere and the cached address is stale, so
+// this entry point must not be called on a device after it has been reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -40,7 +43,11 @@ extern "C" int elf_estimate_weights_noalloc(const float* I, int n_led, int n_low
   if (!I || !weights) return elf::noalloc_set_error(ELF_EINVAL, "null I or weights");
   if (n_led < 1 || n_lowres < 3 || n_lowres > 4096 || (fidelity != 0 && fidelity != 1))
     return elf::noalloc_set_error(ELF_EINVAL, "n_led must be >= 1, n_lowres in [3, 4096], fidelity 0 or 1");
-  const long long parts = (long long)elf::alpha_blocks(n_led, n_lowres);
+  // one partial per (image, 16-row chunk of the interior), counted in 64 bits: every image needs at least
+  // one, so n_led alone already bounds the count from below
+  const long long parts = n_led > ELF_NOALLOC_WEIGHT_MAX_PARTIALS
+                              ? (long long)n_led
+                              : (long long)n_led * (long long)((n_lowres - 2 + 15) / 16);
   if (parts > ELF_NOALLOC_WEIGHT_MAX_PARTIALS)
     return elf::noalloc_set_error(
         ELF_EINVAL, ("problem too large for the static scratch: needs " + std::to_string(parts) +

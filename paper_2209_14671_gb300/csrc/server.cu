@@ -75,7 +75,7 @@ std::string make_key(const elf_problem& p, const elf_options& o) {
 }
 
 // Device bytes a handle of this problem will hold (the allocations of elf_create).
-size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity) {
+size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity, int tile_path) {
   const size_t n = p.n_lowres, N = (size_t)p.n_lowres * p.upsample, K = p.n_led;
   const size_t M = p.n_mux <= 0 ? 1 : p.n_mux, nI = K / M;  // measured images
   const size_t A = N * N, B = n * n, S = B;  // the support is at most the whole pupil grid
@@ -91,8 +91,10 @@ size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity) {
   const size_t gmap = fidelity >= 1 ? 4 * nI * B : 0;
   // multiplexed images: per-LED |o|^2, per-image residual and factor, per-block cost partials
   const size_t mux = M > 1 ? 4 * K * B + 8 * nI * B + 8 * nI * (size_t)elf::mux_blocks_per_image((int)n) : 0;
+  // the split tile path keeps two support bands per LED (at most n rows of n complex each)
+  const size_t split = elf::tile_split_selected((int)n, (int)M, tile_dft, tile_path) ? 16 * K * B : 0;
   return 8 * A * 7 + 4 * A * 2 + 4 * nI * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + gmap +
-         mux + (1u << 20);
+         mux + split + (1u << 20);
 }
 
 }  // namespace
@@ -153,7 +155,7 @@ int admit_one(elf_server s) {
     p = it->second;
     s->idle.erase(it);
   } else {
-    const size_t est = estimate_bytes(r->prob, r->opt.tile_dft, r->opt.fidelity);
+    const size_t est = estimate_bytes(r->prob, r->opt.tile_dft, r->opt.fidelity, r->opt.tile_path);
     if (!make_room(s, est)) return 0;
     if (cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail(ELF_ECUDA, "cudaStreamCreate failed");
@@ -207,7 +209,7 @@ int elf_server_submit(elf_server s, const elf_problem* prob, const elf_options* 
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
   for (Request* q : s->active)
     if (q->tag == tag) return fail(ELF_EINVAL, "tag already in use");
-  if (estimate_bytes(*prob, opt ? opt->tile_dft : 0, opt ? opt->fidelity : 0) > s->budget)
+  if (estimate_bytes(*prob, opt ? opt->tile_dft : 0, opt ? opt->fidelity : 0, opt ? opt->tile_path : 0) > s->budget)
     return fail(ELF_ENOMEM, "request larger than the memory budget");
   Request* r = new Request();
   r->tag = tag;

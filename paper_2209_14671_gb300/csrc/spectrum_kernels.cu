@@ -411,8 +411,8 @@ cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s) {
 // other half of the double-buffered pair (the gather and pupil kernels still read this one).
 __global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, int nfid, const float2* fidff, int nff,
                                                            const double* hp, int nh, double* ring,
-                                                           int* t_dev, double* out3, float* bc_next, double* gp,
-                                                           double g1, double g2) {
+                                                           int* t_dev, double* out4, const double* weights, float* bc_next,
+                                                           double* gp, double g1, double g2) {
   // per-thread sums over a fixed stride (FP64 partials in FP64, (hi, lo) pairs as pairs),
   // then one block sum of (hi, lo) pairs
   __shared__ float red[2 * 3 * 32];
@@ -440,10 +440,11 @@ __global__ void __launch_bounds__(1024) cost_reduce_kernel(const double* fid, in
   block_sum_ff<3>(part, red, sum);
   const double a0 = sum[0], a1 = sum[1], a2 = sum[2];
   if (threadIdx.x == 0) {
-    if (out3) {
-      out3[0] = a0;
-      out3[1] = a1;
-      out3[2] = a2;
+    if (out4) {  // the three terms and Eq. 8's total L = L_fid + alpha L_A + beta L_Phi, in FP64
+      out4[0] = a0;
+      out4[1] = a1;
+      out4[2] = a2;
+      out4[3] = a0 + weights[0] * a1 + weights[1] * a2;
     }
     if (ring) {
       const int t = *t_dev;
@@ -478,9 +479,10 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
 }
 
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
-                               double* ring, int* t_dev, double* out3, float* bc_next, double* gp, double g1,
-                               double g2, cudaStream_t s) {
-  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out3, bc_next, gp, g1, g2);
+                               double* ring, int* t_dev, double* out4, const double* weights, float* bc_next,
+                               double* gp, double g1, double g2, cudaStream_t s) {
+  cost_reduce_kernel<<<1, 1024, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out4, weights, bc_next, gp, g1,
+                                        g2);
   return cudaGetLastError();
 }
 

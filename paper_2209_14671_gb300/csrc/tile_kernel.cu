@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   const int warp = tid >> 5, wl = tid & 31;
   int crank = 0;
   if constexpr (CS > 1) crank = (int)cg::this_cluster().block_rank();
-  const int led = blockIdx.x / CS;
+  const int led = a.led0 + (int)blockIdx.x / CS;
   const int lane = tid % TL;
   const int team = tid / TL;
   const int x0 = crank * CW;
@@ -553,7 +553,7 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
   constexpr int CS = TileCfg<NL>::CS, NT = TileCfg<NL>::NT;
   const size_t smem = tile_smem_bytes(NL, CS, a.rowsA);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(a.K * CS);
+  cfg.gridDim = dim3((a.nled > 0 ? a.nled : a.K) * CS);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;

@@ -32,7 +32,8 @@ class ElfOptions(ctypes.Structure):
     _fields_ = [("fidelity", c_int), ("omega_iso", c_int), ("learn_pupil", c_int), ("pupil_filter", c_int),
                 ("alpha", c_double), ("beta", c_double), ("gamma1", c_double), ("gamma2", c_double),
                 ("s0_psi", c_double), ("s0_pupil", c_double), ("eta_opt", c_double), ("eta_h", c_double),
-                ("tau_fid", c_double), ("tau_h", c_double), ("tile_dft", c_int), ("g_exponent", c_double)]
+                ("tau_fid", c_double), ("tau_h", c_double), ("tile_dft", c_int), ("g_exponent", c_double),
+                ("tile_path", c_int)]
 
 
 class ElfDegradeParams(ctypes.Structure):
@@ -80,6 +81,12 @@ SIGNATURES = {
     "elf_noise_level": (c_int, [c_void_p, c_void_p, c_void_p, P_double]),
     "elf_lsnr": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p, P_double]),
     "elf_object_quality": (c_int, [c_void_p, c_void_p, P_double]),
+    "elf_measure_fp32_peak": (c_int, [c_int, c_int, c_void_p, P_double, P_double]),
+    "elf_shard_row_floats": (c_int, [c_void_p]),
+    "elf_shard_tiles": (c_int, [c_void_p, c_int, c_int]),
+    "elf_shard_export": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "elf_shard_import": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "elf_shard_finish": (c_int, [c_void_p]),
     "elf_destroy": (None, [c_void_p]),
     "elf_strerror": (ctypes.c_char_p, [c_int]),
     "elf_last_error": (ctypes.c_char_p, []),
@@ -222,6 +229,25 @@ class Elf:
     def step(self, n_iter: int = 1):
         _check(load().elf_step(self._h, int(n_iter)), "elf_step")
 
+    # ------------------------------------------------------------ LED sharding of one iteration
+    def shard_row_floats(self) -> int:
+        return _check(load().elf_shard_row_floats(self._h), "elf_shard_row_floats")
+
+    def shard_tiles(self, led_begin: int, led_end: int):
+        _check(load().elf_shard_tiles(self._h, int(led_begin), int(led_end)), "elf_shard_tiles")
+
+    def shard_export(self, led_begin: int, led_end: int, out):
+        p, dev = _ptr(out)
+        _check(load().elf_shard_export(self._h, int(led_begin), int(led_end), c_void_p(p), dev), "elf_shard_export")
+        return out
+
+    def shard_import(self, led_begin: int, led_end: int, src):
+        p, dev = _ptr(src)
+        _check(load().elf_shard_import(self._h, int(led_begin), int(led_end), c_void_p(p), dev), "elf_shard_import")
+
+    def shard_finish(self):
+        _check(load().elf_shard_finish(self._h), "elf_shard_finish")
+
     def _get(self, fn, shape, out):
         if out is None:
             out = np.empty(shape, dtype=np.complex64)
@@ -285,12 +311,13 @@ class Elf:
         _check(load().elf_set_state(self._h, ctypes.byref(st), dev), "elf_set_state")
 
     def cost_grad(self, psi, pupil, g_psi=None, g_pupil=None):
-        """(costs[3] float64, g_psi, g_pupil) at (psi, pupil); outputs allocated as NumPy if None."""
+        """(costs float64 [L_fid, L_A, L_Phi, L], g_psi, g_pupil) at (psi, pupil), L the Eq. 8 total
+        summed by the library; outputs allocated as NumPy if None."""
         if g_psi is None:
             g_psi = np.empty((self.N, self.N), np.complex64)
         if g_pupil is None:
             g_pupil = np.empty((self.n, self.n), np.complex64)
-        c = (c_double * 3)()
+        c = (c_double * 4)()
         pp, dev = _ptr(psi)
         pq, _ = _ptr(pupil)
         gp, _ = _ptr(g_psi)
@@ -364,6 +391,16 @@ def estimate_weights_noalloc(I_dev, n_led: int, n_lowres: int, fidelity: int, we
     _check(load().elf_estimate_weights_noalloc(c_void_p(pi), int(n_led), int(n_lowres), int(fidelity),
                                                c_void_p(pw), c_void_p(_stream_handle(stream))),
            "elf_estimate_weights_noalloc")
+
+
+def measure_fp32_peak(iters: int = 32768, repeats: int = 5, stream=None) -> tuple[float, float]:
+    """(TFLOP/s, ms) of the best of `repeats` launches of the library's FP32 FMA-throughput kernel on
+    the current device (synchronises)."""
+    tf = c_double()
+    ms = c_double()
+    _check(load().elf_measure_fp32_peak(int(iters), int(repeats), c_void_p(_stream_handle(stream)), ctypes.byref(tf),
+                                        ctypes.byref(ms)), "elf_measure_fp32_peak")
+    return float(tf.value), float(ms.value)
 
 
 def exported_symbols_from_header(header_path: str) -> list[str]:

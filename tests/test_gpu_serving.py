@@ -4,6 +4,9 @@ A mix of problem shapes arrives while earlier jobs are still on the GPU; every
 result must equal the one-at-a-time plain path bit for bit (each job's
 arithmetic is that of a lone run; nothing is shared between jobs), also when a
 tight memory budget forces requests to wait and idle handles to be evicted.
+At the serving workload's own shapes (n 64/128/256, K 49/121/225) every served
+result is also compared with the FP64 oracle, and the mixed stream must finish
+sooner than the same jobs one at a time.
 """
 import numpy as np
 import pytest
@@ -11,7 +14,10 @@ import pytest
 import oracle as O
 from paper_2209_14671_gb300 import build as B
 from paper_2209_14671_gb300 import elfpie as E
+from paper_2209_14671_gb300 import inputs as IN
 from paper_2209_14671_gb300 import serve as S
+
+from _cases import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +93,60 @@ def test_server_error_paths(requests):
         with pytest.raises(E.ElfError) as ei:   # cannot fit even alone
             srv.submit(1, r["n"], r["u"], r["k_xy"], r["na"], r["wl"], r["dx"], r["I"], r["n_iter"])
         assert ei.value.code == E.ELF_ENOMEM
+
+
+# ------------------------------------------------------------------ the serving workload's own shapes
+CONFIG4 = [(n, g) for n in (64, 128, 256) for g in (7, 11, 15)]  # n x LED grid (K = 49, 121, 225)
+ORACLE_ITERS = 4
+
+
+def _config4_request(n, grid, seed, n_iter, options=None):
+    """A request of the serving workload: workload-0 optics with an n x n camera and a grid x grid
+    LED array, a seeded smooth object, measurements from the oracle's forward model at the true
+    LED positions plus the workload's Gaussian noise (sigma 1e-3)."""
+    w = IN.problem(0, grid=grid, n=n)
+    geo_true = O.make_geometry(n, w["u"], w["k_xy_true"], w["na"], w["wavelength_um"], w["pixel_um"])
+    obj = IN.object_field(1000 + seed, w)
+    I = O.forward_intensity(O.spectrum_from_object(obj), geo_true.support.astype(complex), geo_true)
+    I = np.ascontiguousarray(IN.corrupt(I, 0, w))
+    return dict(n=n, u=w["u"], k_xy=w["k_xy"].astype(np.float32), na=w["na"], wl=w["wavelength_um"],
+                dx=w["pixel_um"], I=I, n_iter=n_iter, options=options, w=w)
+
+
+def test_served_results_match_oracle_at_serving_shapes():
+    """Every shape of the serving workload (n in {64, 128, 256} x K in {49, 121, 225}) served in one
+    mixed stream; each served object is compared with the FP64 oracle's run of the same request
+    (Algorithm 1 from the initial state) and with the lone run; the stream's makespan must be
+    shorter than the sum of the lone service times (the jobs overlap on the device).
+
+    These requests use beta = 0 (alpha automatic): from the initial state the object is real and
+    Eq. 14's normaliser turns FP32 rounding noise in its zero phase into a step that no FP32 run
+    shares with FP64 (tests/golden/fp32_spread_w0.json); without the phase term the served run
+    must follow the oracle to the full-run bound 1e-4."""
+    B.build()
+    E.load()
+    opts = dict(beta=0.0)
+    checked = [_config4_request(n, g, seed=i, n_iter=ORACLE_ITERS, options=opts) for i, (n, g) in enumerate(CONFIG4)]
+    # small latency-bound jobs around them, to show overlap
+    fill = [_config4_request(64, 7, seed=50 + i, n_iter=12) for i in range(12)]
+    reqs = checked + fill
+    S.run_serial(reqs)                                  # warm-up of the serial path (lazy loading)
+    serial_t, _, lone = S.run_serial(reqs)              # service times exclude handle creation
+    with S.Server(budget_bytes=16 << 30, max_active=16) as srv:
+        S.run_stream(srv, reqs, np.zeros(len(reqs)))   # warm-up: a pooled handle and graphs per shape
+        _, makespan, mixed = S.run_stream(srv, reqs, np.zeros(len(reqs)), collect=True)
+    print(f"serving shapes: makespan {makespan * 1e3:.1f} ms vs sum of lone service times "
+          f"{serial_t.sum() * 1e3:.1f} ms")
+    for i in range(len(reqs)):
+        assert np.array_equal(mixed[i], lone[i]), i
+    assert makespan < serial_t.sum()
+    for i, r in enumerate(checked):
+        w = r["w"]
+        geo = O.make_geometry(r["n"], r["u"], w["k_xy"], r["na"], r["wl"], r["dx"])
+        opt = O.Options(beta=0.0)
+        I = r["I"].astype(np.float64)
+        st = O.init_state(I, geo, w["k_xy"], opt)
+        ref, _ = O.run(st, I, geo, opt, r["n_iter"])
+        e = rel(mixed[i], O.object_from_spectrum(ref.psi))
+        print(f"n={r['n']} K={geo.K}: served object vs FP64 oracle after {r['n_iter']} iterations {e:.2e}")
+        assert e < 1e-4, (r["n"], geo.K, e)

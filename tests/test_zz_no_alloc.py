@@ -45,11 +45,19 @@ def test_noalloc_weights_match_handle_path_on_two_calls(torch_dev, name, fidelit
     K, n = c["I"].shape[0], c["I"].shape[1]
     for call in range(2):
         out.fill_(-1.0)
+        torch.cuda.synchronize(dev)
+        before = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
         E.estimate_weights_noalloc(I_dev, K, n, fidelity, out, stream)
         torch.cuda.synchronize(dev)
+        after = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
         a, b = out.cpu().tolist()
         assert a == b
         assert abs(a - a_ref) <= TOL_ALPHA * abs(a_ref), (call, a, a_ref)
+        if call == 1:
+            # A coarse check of the claim itself: the first call may load the module, the second must
+            # leave torch's allocator and the device's free memory (cudaMemGetInfo) exactly as they were.
+            # It would not see an allocation freed again within the call.
+            assert after == before, (before, after)
 
 
 def test_noalloc_rejects_problems_beyond_the_static_scratch(torch_dev):
