@@ -422,7 +422,9 @@ bool tile_split_selected(int n, int mux, int tile_dft, int tile_path) {
   if (mux > 1 || tile_dft) return false;
   if (tile_path == 2) return true;
   if (tile_path == 1) return false;
-  return false;  // automatic: the cluster kernel
+  // automatic: measured on GB300 (tile stage of the 225-LED workloads), the split kernels take 150 us
+  // against 217 us at n = 256; at n = 128 and 64 the cluster kernel is as fast or faster
+  return n >= 256;
 }
 
 cudaError_t prepare_tile_split(int n) {

@@ -384,3 +384,26 @@ def test_plain_l1_tau_zero(name, iso):
              cost=float(np.max(np.abs(costs - np.asarray(costs_ref)) / np.asarray(costs_ref))))
     print(name, variant, " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["cost"] < TOL_FWD
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("variant", [dict(), dict(fidelity=1, omega_iso=0), dict(fidelity=2, g_exponent=0.375)])
+def test_tile_paths_agree(name, variant):
+    """The two kernel layouts of the tile work (tile_path 1: one cluster per LED with the tile on
+    chip; 2: row / column-and-stencil / row kernels through device memory) do the same per-element
+    arithmetic on the same state: the tile gradients and both gradients are bitwise equal; the costs,
+    whose per-CTA pairs are added in a different order, agree to 1e-8."""
+    c = case(name)
+    st = developed_state(name)
+    out = {}
+    for path in (1, 2):
+        with make_elf(c, tile_path=path, **variant) as elf:
+            elf.set_measurements(c["I"])
+            load_state(elf, st)
+            costs, g_psi, g_pup = elf.cost_grad(st.psi.astype(np.complex64), st.pupil.astype(np.complex64))
+            out[path] = (costs, g_psi, g_pup, elf.get_tile_grads())
+    (c1, gp1, gq1, G1), (c2, gp2, gq2, G2) = out[1], out[2]
+    e = dict(G=rel(G2, G1), g_psi=rel(gp2, gp1), g_p=rel(gq2, gq1), cost=float(np.max(np.abs(c2 - c1) / np.abs(c1))))
+    print(name, variant, "split vs cluster:", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert np.array_equal(G1, G2) and np.array_equal(gp1, gp2) and np.array_equal(gq1, gq2)
+    assert e["cost"] < 1e-8

@@ -8,6 +8,9 @@ about 2^-16 relative; sums over 64-128 terms keep the tile transforms within
 1e-4, state after one iteration from a developed state 1e-5 (the update
 contracts gradient errors by |Delta Psi| / |Psi|).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -18,6 +21,13 @@ from paper_2209_14671_gb300 import elfpie as E
 from _cases import case, load_state, oracle_state_to_f32, rel
 
 pytestmark = pytest.mark.gpu
+
+
+def _spread(model, at):
+    """The FP64 oracle's own spread on this workload under the given noise model (largest of the
+    seeded perturbed runs), written by tests/golden/make_fp32_spread.py."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fp32_spread_w3.json")
+    return json.load(open(path))["spread"][model][str(at)]["max"]
 
 
 @pytest.fixture(scope="module")
@@ -84,12 +94,14 @@ def test_full_run_against_oracle(w3):
     """The workload's full run (200 iterations, after the 3 of the developed state) on both tile
     paths; relative L2 of Psi and P against the FP64 oracle, reported every 50 iterations.
 
-    The iteration amplifies small state differences: in the FP64 oracle alone a 1e-7 relative
-    perturbation of Psi and P (FP32 rounding) grows to 1.6e-5 after 50 iterations, so FP32 runs
-    drift from FP64 by more than their per-iteration error. Measured: FFT path Psi 1.4e-4 at 50
-    iterations, 3.4e-5 at 200 (the trajectory converges), P 2.2e-4 at 200; tensor-core path Psi
-    4.6e-5 and P 1.6e-3 at 200. Bounds on the final state: Psi 1e-4 (FFT) and 2e-4 (tensor
-    cores), P 5e-4 and 3e-3."""
+    The iteration amplifies small state differences, so a run drifts from FP64 by more than its
+    per-iteration error.  The FP64 oracle itself, with noise of the FP32 path's rounding size
+    injected into its state and its object, ends 200 iterations at a spread of Psi 1.2e-4 and
+    P 4.9e-4 from the noiseless run; with the tensor-core model's noise (2e-5 of every LED field
+    as well) at Psi 2.9e-4 and P 1.1e-2 (tests/golden/fp32_spread_w3.json).  Bounds on the final
+    state: FFT path Psi 1e-4 (the full-run bound of the contract, which this run meets) and P twice
+    the FP32 spread; tensor-core path Psi twice its spread and P 3e-3, tighter than twice its spread,
+    as a guard on the measured 1.6e-3."""
     c, st, opt = w3
     I = c["I"].astype(np.float64)
     refs = {}
@@ -108,8 +120,10 @@ def test_full_run_against_oracle(w3):
                 errs[(td, it)] = (rel(s["psi"], refs[it].psi), rel(s["pupil"], refs[it].pupil))
                 print(f"tile_dft={td} after {it} iterations: psi {errs[(td, it)][0]:.2e} "
                       f"pupil {errs[(td, it)][1]:.2e}")
-    assert errs[(0, 200)][0] < 1e-4 and errs[(0, 200)][1] < 5e-4
-    assert errs[(1, 200)][0] < 2e-4 and errs[(1, 200)][1] < 3e-3
+    sp32 = _spread("fp32", 200)
+    sptc = _spread("tc", 200)
+    assert errs[(0, 200)][0] < 1e-4 and errs[(0, 200)][1] < 2.0 * sp32["pupil"]
+    assert errs[(1, 200)][0] < 2.0 * sptc["psi"] and errs[(1, 200)][1] < 3e-3
 
 
 @pytest.mark.parametrize("variant", [dict(fidelity=2, g_exponent=0.375), dict(fidelity=3)])
