@@ -36,8 +36,8 @@ from paper_2209_14671_gb300 import inputs as IN  # noqa: E402
 METRIC = "LED sub-image updates/s (K×iters/s) at fixed error vs FP64 oracle; p99 latency"
 UNIT = "LED sub-image updates/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_PATH = os.path.join(ROOT, "profiles", "tile_kernel_traffic.json")
-TILE_SOURCES = ["paper_2209_14671_gb300/csrc/tile_kernel.cu", "paper_2209_14671_gb300/csrc/fft.cuh",
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "tile_stage_traffic.json")
+TILE_SOURCES = ["paper_2209_14671_gb300/csrc/tile_split.cu", "paper_2209_14671_gb300/csrc/fft.cuh",
                 "paper_2209_14671_gb300/csrc/reduce.cuh"]
 L2_FLUSH_BYTES = 256 << 20
 
@@ -688,7 +688,9 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
                        "learn_pupil": 1, "fidelity": "intensity (Eq. 5)"},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tf / alu_peak, "traffic": traffic, "kernel": "tile_kernel<256,8>",
+                         "frac": achieved_tf / alu_peak, "traffic": traffic,
+                         "kernel": "tile stage (the per-LED work of Eqs. 1, 5, 12, 11, F_B^H): rows_inv_kernel<256> + "
+                                   "cols_kernel<256,0,1> + rows_fwd_kernel<256>, one launch each per iteration",
                          "algorithmic_flops": tile_flops, "launch_ms": tile_ms, "peak_source": alu_src,
                          "flop_model": "per LED: two n x n 2D FFTs at 5 B log2 B each + 40 FLOP per pixel",
                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

@@ -91,7 +91,7 @@ typedef struct {
   int tile_dft;      /* tile transforms: 0 = FP32 FFT (default); 1 = tensor-core DFT, BF16 3-term split with
                         FP32 accumulation (not in the paper; n_lowres = 128 with the support band <= 64 only) */
   double g_exponent; /* gamma of the power map (fidelity 2), in (0, 8]; 1 by default (Sec. 6.3) */
-  int tile_path;     /* kernels of the FP32 tile work (same arithmetic): 0 = automatic (default: 2 for n_lowres = 256,
+  int tile_path;     /* kernels of the FP32 tile work (same arithmetic): 0 = automatic (default: 2 for n_lowres >= 128,
                         else 1), 1 = one thread-block
                         cluster per LED, the tile kept on chip; 2 = three kernels per iteration (inverse row
                         transforms, column transforms + the stencil of Eqs. 5, 12, 11, forward row transforms) that

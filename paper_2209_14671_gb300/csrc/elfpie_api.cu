@@ -100,6 +100,7 @@ struct elf_handle_s {
   float *v_p = nullptr, *delta_p = nullptr;
   // scratch
   float2 *G = nullptr, *ot = nullptr, *q = nullptr, *small = nullptr, *part = nullptr;
+  float2* fft_tmp = nullptr;  // scratch of the N x N transforms (four-step column passes), N >= 256
   int* pdone = nullptr;  // per 256 support pixels: Eq. 18 chunks finished (reset by the partial kernel)
   float2 *psi_eval = nullptr, *pupil_eval = nullptr, *g_psi = nullptr, *g_p = nullptr, *pupil_unit = nullptr;
   float2* cost_ff = nullptr;  // per-warp (hi, lo) fidelity cost partials of the tile kernel
@@ -214,13 +215,39 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   pa.eta = (float)h->opt.eta_opt;
   pa.mode = mode;
   pa.done = h->pdone;
+  GatherArgs ga{};
+  ga.G = h->G;
+  ga.pupil = pupil;
+  ga.origin = h->origin;
+  ga.row_xs = h->row_xs;
+  ga.row_cnt = h->row_cnt;
+  ga.row_off = h->row_off;
+  ga.seg_ptr = h->seg_ptr;
+  ga.seg_ent = h->seg_ent;
+  ga.gH = h->q;
+  ga.psi = psi;
+  ga.psi_out = psi_out;
+  ga.mu = h->mu_psi;
+  ga.v = h->v_psi;
+  ga.delta = h->delta_psi;
+  ga.g_out = h->g_psi;
+  ga.bc = bc_cur;
+  ga.N = h->N;
+  ga.n = h->n;
+  ga.S = h->S;
+  ga.K = h->K;
+  ga.tiles_x = h->tiles_x;
+  ga.g1 = (float)h->opt.gamma1;
+  ga.g2 = (float)h->opt.gamma2;
+  ga.eta = (float)h->opt.eta_opt;
+  ga.mode = mode;
   if (parts & kPartFront) {
     ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
     // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
     ELF_CK(cudaEventRecord(h->ev_fork, s0));
     ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
-    ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi));  // the first pass reads Psi, writes ot
+    ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi, h->fft_tmp));  // the first pass reads Psi
     HessArgs ha{};
     ha.ot = h->ot;
     ha.q = h->q;
@@ -232,7 +259,7 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ha.eta = (float)h->opt.eta_h;
     ha.iso = h->opt.omega_iso;
     ELF_CK(launch_hessian(ha, h->aux));
-    ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux));
+    ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux, nullptr, h->fft_tmp));
     ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
     ELF_CK(cudaEventRecord(h->ev_join, h->aux));
 
@@ -364,32 +391,6 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   }
 
   ELF_CK(cudaStreamWaitEvent(s0, h->ev_join, 0));
-  GatherArgs ga{};
-  ga.G = h->G;
-  ga.pupil = pupil;
-  ga.origin = h->origin;
-  ga.row_xs = h->row_xs;
-  ga.row_cnt = h->row_cnt;
-  ga.row_off = h->row_off;
-  ga.seg_ptr = h->seg_ptr;
-  ga.seg_ent = h->seg_ent;
-  ga.gH = h->q;
-  ga.psi = psi;
-  ga.psi_out = psi_out;
-  ga.mu = h->mu_psi;
-  ga.v = h->v_psi;
-  ga.delta = h->delta_psi;
-  ga.g_out = h->g_psi;
-  ga.bc = bc_cur;
-  ga.N = h->N;
-  ga.n = h->n;
-  ga.S = h->S;
-  ga.K = h->K;
-  ga.tiles_x = h->tiles_x;
-  ga.g1 = (float)h->opt.gamma1;
-  ga.g2 = (float)h->opt.gamma2;
-  ga.eta = (float)h->opt.eta_opt;
-  ga.mode = mode;
   ELF_MARK(s0, ELF_STAGE_GATHER, 0);
   ELF_CK(launch_gather(ga, s0));
   ELF_MARK(s0, ELF_STAGE_GATHER, 1);
@@ -708,6 +709,7 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->G, (size_t)K * S))) return rc;
   if ((rc = dalloc(h, &h->ot, A))) return rc;
   if ((rc = dalloc(h, &h->q, A))) return rc;
+  if (N >= 256 && (rc = dalloc(h, &h->fft_tmp, A))) return rc;
   if ((rc = dalloc(h, &h->small, B))) return rc;
   if ((rc = dalloc(h, &h->part, (size_t)h->Q * S))) return rc;
   if ((rc = dalloc(h, &h->pdone, (size_t)(S + 255) / 256))) return rc;
@@ -815,7 +817,7 @@ int handle_set_measurements_async(elf_handle h, const float* I) {
 
 int handle_get_object_async(elf_handle h, float* obj) {
   const size_t A = (size_t)h->N * h->N;
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi));  // reads Psi, writes ot
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi, h->fft_tmp));  // reads Psi, writes ot
   ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
   ELF_CK(cudaMemcpyAsync(obj, h->ot, A * sizeof(float2), cudaMemcpyDefault, h->user));
   return ELF_OK;
@@ -974,7 +976,7 @@ int elf_get_object(elf_handle h, float* obj, int is_device) {
   if (!obj) return set_error(ELF_EINVAL, "null output");
   (void)is_device;
   const size_t A = (size_t)h->N * h->N;
-  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi));  // reads Psi, writes ot
+  ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->user, h->psi, h->fft_tmp));  // reads Psi, writes ot
   ELF_CK(launch_sign_scale(h->ot, h->ot, h->N, (float)(1.0 / (double)A), h->user));
   return copy_out(h, obj, h->ot, A * sizeof(float2));
 }
@@ -1096,7 +1098,7 @@ int elf_simulate(elf_handle h, const float* obj, float* I_out, int is_device) {
   // Psi = fftshift(DFT_N(O)) = DFT_N((-1)^(x+y) O)
   ELF_CK(cudaMemcpyAsync(h->psi_eval, obj, A * 8, cudaMemcpyDefault, s));
   ELF_CK(launch_sign_scale(h->psi_eval, h->psi_eval, h->N, 1.f, s));
-  ELF_CK(launch_fft2(h->psi_eval, h->N, false, h->tw_N, s));
+  ELF_CK(launch_fft2(h->psi_eval, h->N, false, h->tw_N, s, nullptr, h->fft_tmp));
   const size_t nI = (size_t)h->n_img * B;  // K/M images of Eq. 1
   float* dst = I_out;
   float* staging = nullptr;

@@ -1,9 +1,14 @@
-// Two-pass 2D FFT of an L x L complex array (the F_A of Eqs. 6-7, 13-14 and
-// the object <-> spectrum maps).  Pass 1 transforms rows: each team of a CTA
-// loads one row with coalesced float2 loads into shared memory, transforms it and
-// writes it back.  Pass 2 transforms columns: a CTA loads an L x CW strip
-// (coalesced CW-wide row segments), stores it column-major with a padded pitch,
-// transforms each column and writes the strip back.
+// 2D FFT of an L x L complex array (the F_A of Eqs. 6-7, 13-14 and the object <-> spectrum maps).
+// Rows: each team of a CTA loads one row with coalesced float2 loads, transforms it and writes it
+// back.  Columns, with a scratch array (the L x L transforms of the iteration): the four-step split
+// L = P * Q of the column index in two passes without shared memory, one thread per (column,
+// sub-transform) and a warp on 32 adjacent columns, so every access is a whole row segment:
+//   pass A  thread (x, n2): the P-point DFT over rows Q n1 + n2 (n1 < P), times W_L^(n2 k1),
+//           into scratch rows n2 P + k1;
+//   pass B  thread (x, k1): the Q-point DFT over scratch rows n2 P + k1 (n2 < Q), giving
+//           X[k1 + P k2] in row k1 + P k2.
+// Without a scratch array a CTA loads an L x CW strip (coalesced CW-wide row segments), stores it
+// column-major with a padded pitch, transforms each column and writes the strip back.
 #include "fft.cuh"
 #include "internal.cuh"
 
@@ -116,10 +121,51 @@ __global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float
   }
 }
 
+// Column passes of the four-step split (see the top of the file); blocks of 32 columns x 4 sub-transforms.
+// twg[k1 * Q + n2] = W_L^(n2 k1) (forward sign), the team twiddle table of fft.cuh.
 template <int L, bool INV>
-static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src) {
+__global__ void __launch_bounds__(128) fft_cols_a_kernel(const float2* __restrict__ data, float2* __restrict__ tmp,
+                                                         const float2* __restrict__ twg) {
+  constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int n2 = blockIdx.y * 4 + threadIdx.y;
+  float2 v[P];
+#pragma unroll
+  for (int n1 = 0; n1 < P; ++n1) v[n1] = data[(size_t)(Q * n1 + n2) * L + x];
+  Dft<P, INV>::run(v);
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) {
+    float2 w = twg[k1 * Q + n2];
+    if (INV) w.y = -w.y;
+    tmp[(size_t)(n2 * P + k1) * L + x] = k1 ? cmul(v[k1], w) : v[k1];
+  }
+}
+
+template <int L, bool INV>
+__global__ void __launch_bounds__(128) fft_cols_b_kernel(const float2* __restrict__ tmp, float2* __restrict__ data) {
+  constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int k1 = blockIdx.y * 4 + threadIdx.y;
+  float2 v[Q];
+#pragma unroll
+  for (int n2 = 0; n2 < Q; ++n2) v[n2] = tmp[(size_t)(n2 * P + k1) * L + x];
+  Dft<Q, INV>::run(v);
+#pragma unroll
+  for (int k2 = 0; k2 < Q; ++k2) data[(size_t)(k1 + P * k2) * L + x] = v[k2];
+}
+
+template <int L, bool INV>
+static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src, float2* tmp) {
   using G = FftGrid<L>;
   fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(src ? src : data, data, tw);
+  if constexpr (L >= 256) {
+    if (tmp) {
+      constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
+      fft_cols_a_kernel<L, INV><<<dim3(L / 32, Q / 4), dim3(32, 4), 0, s>>>(data, tmp, tw);
+      fft_cols_b_kernel<L, INV><<<dim3(L / 32, P / 4), dim3(32, 4), 0, s>>>(tmp, data);
+      return cudaGetLastError();
+    }
+  }
   fft_cols_kernel<L, INV><<<(L + G::CPC - 1) / G::CPC, G::COL_THREADS, G::COL_SMEM, s>>>(data, tw);
   return cudaGetLastError();
 }
@@ -154,10 +200,11 @@ cudaError_t prepare_fft(int L) {
 #undef ELF_PREP_CASE
 }
 
-cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s, const float2* src) {
+cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s, const float2* src,
+                        float2* tmp) {
 #define ELF_FFT_CASE(LL)                                                     \
   case LL:                                                                   \
-    return inverse ? fft2_t<LL, true>(data, tw, s, src) : fft2_t<LL, false>(data, tw, s, src);
+    return inverse ? fft2_t<LL, true>(data, tw, s, src, tmp) : fft2_t<LL, false>(data, tw, s, src, tmp);
   switch (L) {
     ELF_FFT_CASE(16)
     ELF_FFT_CASE(32)

@@ -79,7 +79,7 @@ size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity, int tile
   const size_t n = p.n_lowres, N = (size_t)p.n_lowres * p.upsample, K = p.n_led;
   const size_t M = p.n_mux <= 0 ? 1 : p.n_mux, nI = K / M;  // measured images
   const size_t A = N * N, B = n * n, S = B;  // the support is at most the whole pupil grid
-  // Psi-sized: 7 complex (Psi double-buffered) + 2 real; per LED: I and G plus the Eq. 18 partials and the tile kernel's
+  // Psi-sized: 8 complex (Psi double-buffered, the transforms' scratch) + 2 real; per LED: I and G plus the Eq. 18 partials and the tile kernel's
   // per-warp cost pairs; pupil-sized: 8 complex + 3 real/int; 1 MB for the remaining tables,
   // twiddles and reductions
   const size_t cost_pairs = 8 * (size_t)elf::tile_cluster_size((int)n) * (size_t)elf::tile_warps((int)n);
@@ -93,7 +93,7 @@ size_t estimate_bytes(const elf_problem& p, int tile_dft, int fidelity, int tile
   const size_t mux = M > 1 ? 4 * K * B + 8 * nI * B + 8 * nI * (size_t)elf::mux_blocks_per_image((int)n) : 0;
   // the split tile path keeps two support bands per LED (at most n rows of n complex each)
   const size_t split = elf::tile_split_selected((int)n, (int)M, tile_dft, tile_path) ? 16 * K * B : 0;
-  return 8 * A * 7 + 4 * A * 2 + 4 * nI * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + gmap +
+  return 8 * A * 8 + 4 * A * 2 + 4 * nI * B + 16 * K * S + cost_pairs * K + 8 * B * 8 + 4 * B * 3 + tc + gmap +
          mux + split + (1u << 20);
 }
 

@@ -32,6 +32,7 @@ constexpr int kRowThreads = 256;
 template <int NL> struct SplitCfg {
   static constexpr int CW = NL < 32 ? NL : 32;  // owned columns per column CTA
   static constexpr int NT = NL >= 256 ? 288 : NL >= 64 ? 288 : 256;
+  static constexpr int MINB = 2;               // column CTAs per SM the registers are bounded for
 };
 
 // Row pitch (in float2) of the column buffer: at least the CW + 2 owned and halo columns, chosen
@@ -154,7 +155,7 @@ size_t cols_smem_bytes() {
 // (power or log by a.fidelity; meas holds g(max(I, 0))); ISO: isotropic (1) or anisotropic (0)
 // normaliser of Eq. 12.
 template <int NL, int FID, int ISO>
-__global__ void __launch_bounds__(SplitCfg<NL>::NT, 2)
+__global__ void __launch_bounds__(SplitCfg<NL>::NT, SplitCfg<NL>::MINB)
     cols_kernel(const TileArgs a, const float2* __restrict__ band_in, float2* __restrict__ band_out) {
   constexpr int CW = SplitCfg<NL>::CW, NT = SplitCfg<NL>::NT, NW = NT / 32;
   constexpr int STRIPS = NL / CW;
@@ -422,9 +423,10 @@ bool tile_split_selected(int n, int mux, int tile_dft, int tile_path) {
   if (mux > 1 || tile_dft) return false;
   if (tile_path == 2) return true;
   if (tile_path == 1) return false;
-  // automatic: measured on GB300 (tile stage of the 225-LED workloads), the split kernels take 150 us
-  // against 217 us at n = 256; at n = 128 and 64 the cluster kernel is as fast or faster
-  return n >= 256;
+  // automatic: measured on GB300 with 225 LEDs, an iteration takes 0.166 against 0.233 ms at n = 256
+  // and 0.054 against 0.059 ms at n = 128 (8-iteration graphs) with the split kernels; at n = 64 the
+  // two are within 2 %, and the cluster kernel is kept there
+  return n >= 128;
 }
 
 cudaError_t prepare_tile_split(int n) {
