@@ -158,7 +158,7 @@ template <int L, bool INV>
 static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src, float2* tmp) {
   using G = FftGrid<L>;
   fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(src ? src : data, data, tw);
-  if constexpr (L >= 256) {
+  if constexpr (L >= 512) {  // at 256 the strip kernel's one launch is faster (64/256/49: 28.5 vs 29.1 us)
     if (tmp) {
       constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
       fft_cols_a_kernel<L, INV><<<dim3(L / 32, Q / 4), dim3(32, 4), 0, s>>>(data, tmp, tw);

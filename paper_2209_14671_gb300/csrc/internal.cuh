@@ -99,7 +99,7 @@ inline int fft_padded_length(int L) { return L + L / fft_team_lanes(L); }
 // 2D transforms of an L x L array: rows pass then columns pass, unnormalised.
 cudaError_t prepare_fft(int L);               // sets kernel attributes; call outside capture
 // src != null: the input is read from src and the result written to data (src is not modified).
-// tmp != null (an L x L scratch array, L >= 256): the column transform runs as the two register passes
+// tmp != null (an L x L scratch array, L >= 512): the column transform runs as the two register passes
 // of the four-step split instead of the shared-memory strip kernel.
 cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s,
                         const float2* src = nullptr, float2* tmp = nullptr);
