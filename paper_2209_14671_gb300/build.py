@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libelfpie.so")
 SOURCES = ["elfpie_api.cu", "tile_kernel.cu", "fft_kernels.cu", "spectrum_kernels.cu", "noalloc.cu",
            "server.cu", "tc_dft.cu", "mux_kernels.cu",
            "eval_kernels.cu", "peak.cu", "tile_split.cu"]
-HEADERS = ["fft.cuh", "internal.cuh", "reduce.cuh"]
+HEADERS = ["dsmem.cuh", "fft.cuh", "internal.cuh", "reduce.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -1,5 +1,6 @@
 // Spectrum-sized kernels of one Elfpie iteration and its set-up:
-//   hessian_kernel   Eqs. 6-7 costs and the object-domain factors of Eqs. 13-14
+//   hessian_kernel   Eqs. 6-7 costs and the object-domain factors of Eqs. 13-14 (tiles in shared
+//                    memory; hessian_walk_kernel: the same per column in registers, from N = 512)
 //   gather_kernel    Eq. 9's sum over LEDs (fixed ascending order, no atomics)
 //                    fused with the Eq. 19 update of Psi (g = Eq. 15)
 //   pupil kernels    Eq. 18 in fixed LED chunks, the 3x3 Gaussian smoothing of P
@@ -160,11 +161,182 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   }
 }
 
-int hess_blocks(int N) { return ((N + HT - 1) / HT) * ((N + HT - 1) / HT); }
+// The same computation without shared memory, so that its blocks fit beside the tile kernels' on one SM.
+// Each thread owns one column and walks a strip of ROWS output rows, keeping in registers a 3-row
+// window of a = |O| and phi = atan2(O) (with the left and right neighbours' values, exchanged by warp
+// shuffles), a 3-row window of omega, and the rows of O it still needs.  A warp spans 32 columns; its
+// 28 inner lanes are outputs and the two outer lanes per side supply the neighbours' a, phi and
+// omega.  Every a and phi is computed once per warp, every omega once, and each pixel's cost is
+// counted by the one lane and row that own it.
+constexpr int kWalkOut = 28;    // output columns per warp
+constexpr int kWalkWarps = 2;   // warps per block: 64 threads fit beside two column CTAs of the tile work
+
+struct WalkAP {  // a and phi of one row at the thread's column and its two neighbours
+  float aL, aM, aR, pL, pM, pR;
+};
+struct WalkW {   // omega of one row (one field): the components Hᵀ needs, with neighbours
+  float xxL, xxM, xxR, yy, xyL, xyR;
+};
+
+__device__ __forceinline__ void walk_ap(const HessArgs& a, int x, int r, WalkAP& o, float2& Or) {
+  const int N = a.N;
+  float am = 0.f, ph = 0.f;
+  Or = make_float2(0.f, 0.f);
+  if (r >= 0 && r < N && x >= 0 && x < N) {
+    float2 v = a.ot[(size_t)r * N + x];
+    const float sg = ((x + r) & 1) ? -a.invA : a.invA;
+    v.x *= sg;
+    v.y *= sg;
+    Or = v;
+    am = sqrtf(cabs2(v));
+    ph = atan2f(v.y, v.x);
+  }
+  o.aM = am;
+  o.pM = ph;
+  o.aL = __shfl_up_sync(0xffffffffu, am, 1);
+  o.aR = __shfl_down_sync(0xffffffffu, am, 1);
+  o.pL = __shfl_up_sync(0xffffffffu, ph, 1);
+  o.pR = __shfl_down_sync(0xffffffffu, ph, 1);
+}
+
+// omega of row r (rows r - 1, r, r + 1 of a and phi given) for both fields; the smoothed cost of the
+// pixel is added when count is set.  Zero outside the interior.
+__device__ __forceinline__ void walk_omega(const HessArgs& a, bool inside, bool count, const WalkAP& u,
+                                           const WalkAP& m, const WalkAP& d, WalkW& wa, WalkW& wp, float& ca,
+                                           float& cp) {
+  const float r2 = 1.41421356237309505f;
+  float h0 = 0.f, h1 = 0.f, h2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  if (inside) {
+    h0 = m.aL - 2.f * m.aM + m.aR;
+    h1 = u.aM - 2.f * m.aM + d.aM;
+    h2 = r2 * 0.25f * (d.aR - d.aL - u.aR + u.aL);
+    const float fa = huber3(h0, h1, h2, a.tau, a.iso);
+    g0 = m.pL - 2.f * m.pM + m.pR;
+    g1 = u.pM - 2.f * m.pM + d.pM;
+    g2 = r2 * 0.25f * (d.pR - d.pL - u.pR + u.pL);
+    const float fp = huber3(g0, g1, g2, a.tau, a.iso);
+    if (count) {
+      ca += fa;
+      cp += fp;
+    }
+  }
+  wa.xxM = h0;
+  wa.yy = h1;
+  wp.xxM = g0;
+  wp.yy = g1;
+  wa.xxL = __shfl_up_sync(0xffffffffu, h0, 1);
+  wa.xxR = __shfl_down_sync(0xffffffffu, h0, 1);
+  wa.xyL = __shfl_up_sync(0xffffffffu, h2, 1);
+  wa.xyR = __shfl_down_sync(0xffffffffu, h2, 1);
+  wp.xxL = __shfl_up_sync(0xffffffffu, g0, 1);
+  wp.xxR = __shfl_down_sync(0xffffffffu, g0, 1);
+  wp.xyL = __shfl_up_sync(0xffffffffu, g2, 1);
+  wp.xyR = __shfl_down_sync(0xffffffffu, g2, 1);
+}
+
+// H^T omega at the middle row of three omega rows.
+__device__ __forceinline__ float walk_ht(const WalkW& u, const WalkW& m, const WalkW& d) {
+  const float dxx = m.xxL - 2.f * m.xxM + m.xxR;
+  const float dyy = u.yy - 2.f * m.yy + d.yy;
+  const float dxy = u.xyL - u.xyR - d.xyL + d.xyR;
+  return dxx + dyy + 1.41421356237309505f * 0.25f * dxy;
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(32 * kWalkWarps) hessian_walk_kernel(const HessArgs a) {
+  __shared__ float red[2 * 2 * kWalkWarps];
+  const int N = a.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x = (blockIdx.x * kWalkWarps + warp) * kWalkOut - 2 + lane;
+  const int y0 = blockIdx.y * ROWS;
+  const bool xint = x >= 1 && x <= N - 2;
+  const bool own = lane >= 2 && lane < 2 + kWalkOut && x < N;
+  const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
+  float ca = 0.f, cp = 0.f;
+  // windows: a / phi of rows y, y + 1, y + 2 (A0, A1, A2), omega of rows y - 1, y, y + 1 (W*0, W*1, W*2),
+  // O of rows y, y + 1, y + 2
+  WalkAP A0, A1, A2, Am;
+  float2 O0, O1, O2, Od;
+  walk_ap(a, x, y0 - 2, Am, Od);
+  walk_ap(a, x, y0 - 1, A0, Od);
+  walk_ap(a, x, y0, A1, O1);
+  walk_ap(a, x, y0 + 1, A2, O2);
+  WalkW Wa0, Wa1, Wa2, Wp0, Wp1, Wp2;
+  {
+    const int r = y0 - 1;
+    walk_omega(a, xint && r >= 1 && r <= N - 2, false, Am, A0, A1, Wa1, Wp1, ca, cp);
+    const int r1 = y0;
+    walk_omega(a, xint && r1 >= 1 && r1 <= N - 2, own && r1 < N, A0, A1, A2, Wa2, Wp2, ca, cp);
+  }
+  // shift: a / phi rows y0 .. y0 + 1 into A0 .. A1, O likewise
+  A0 = A1;
+  A1 = A2;
+  O0 = O1;
+  O1 = O2;
+#pragma unroll 4
+  for (int i = 0; i < ROWS; ++i) {
+    const int y = y0 + i;
+    // a / phi and O of row y + 2
+    walk_ap(a, x, y + 2, A2, O2);
+    // omega of row y + 1 (counted when that row is an output row of this strip)
+    Wa0 = Wa1;
+    Wp0 = Wp1;
+    Wa1 = Wa2;
+    Wp1 = Wp2;
+    const int r = y + 1;
+    walk_omega(a, xint && r >= 1 && r <= N - 2, own && i + 1 < ROWS && r < N, A0, A1, A2, Wa2, Wp2, ca, cp);
+    // q of row y: alpha O / (2 max(a, eta)) H^T omega_a + beta (i/2) O / (a^2 + eta) H^T omega_phi,
+    // times (-1)^(x+y) / A for the forward transform
+    if (own && y < N) {
+      const float ta = walk_ht(Wa0, Wa1, Wa2), tp = walk_ht(Wp0, Wp1, Wp2);
+      const float am = A0.aM;
+      const float2 o = O0;
+      const float sg = ((x + y) & 1) ? -a.invA : a.invA;
+      const float ka = __fdividef(alpha * ta, 2.f * fmaxf(am, a.eta));
+      const float kp = __fdividef(beta * 0.5f * tp, am * am + a.eta);
+      const float2 q = make_float2(ka * o.x - kp * o.y, ka * o.y + kp * o.x);
+      a.q[(size_t)y * N + x] = cscale(q, sg);
+    }
+    A0 = A1;
+    A1 = A2;
+    O0 = O1;
+    O1 = O2;
+  }
+  const float part[2] = {ca, cp};
+  double sum[2];
+  block_sum_ff<2>(part, red, sum);
+  if (threadIdx.x == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    a.costpart[2 * b] = sum[0];
+    a.costpart[2 * b + 1] = sum[1];
+  }
+}
+
+static int walk_cols(int N) { return (((N + kWalkOut - 1) / kWalkOut) + kWalkWarps - 1) / kWalkWarps; }
+
+// Which kernel runs, measured on GB300 in the whole iteration: the tiled kernel at N <= 256 (64/256/49:
+// 29.5 against 30.8 us), the walk with 8-row strips at N = 512 (52.7 against 53.4 us at 128/512/225)
+// and with 16-row strips from N = 1024 (161.0 against 163.0 us at 256/1024/225).  Shorter strips give
+// more warps for latency hiding and cost recomputed halo rows.
+static int walk_rows(int N) { return N <= 256 ? 0 : (N <= 512 ? 8 : 16); }
+
+// Blocks of the launch, each writing one (L_A, L_Phi) cost pair.
+int hess_blocks(int N) {
+  const int r = walk_rows(N);
+  if (r == 0) return ((N + HT - 1) / HT) * ((N + HT - 1) / HT);
+  return walk_cols(N) * ((N + r - 1) / r);
+}
 
 cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s) {
-  const int t = (a.N + HT - 1) / HT;
-  hessian_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(a);
+  const int r = walk_rows(a.N);
+  if (r == 0) {
+    const int t = (a.N + HT - 1) / HT;
+    hessian_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(a);
+  } else if (r == 8) {
+    hessian_walk_kernel<8><<<dim3(walk_cols(a.N), (a.N + 7) / 8), 32 * kWalkWarps, 0, s>>>(a);
+  } else {
+    hessian_walk_kernel<16><<<dim3(walk_cols(a.N), (a.N + 15) / 16), 32 * kWalkWarps, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

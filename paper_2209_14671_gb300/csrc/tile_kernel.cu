@@ -26,6 +26,7 @@
 // 1/(u^2 n^2) is applied to o and to G.
 #include <cooperative_groups.h>
 
+#include "dsmem.cuh"
 #include "fft.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -54,59 +55,6 @@ __host__ __device__ constexpr int oc_pitch(int n) {
 
 // largest power of two <= w (the warps that walk row strips in the stencil pass)
 __host__ __device__ constexpr int pow2_floor(int w) { return w >= 16 ? 16 : w >= 8 ? 8 : w >= 4 ? 4 : w >= 2 ? 2 : 1; }
-
-
-// The two halves of a cluster barrier (no memory ordering: used only to know that every CTA
-// of the cluster is running); every thread of every CTA executes both.
-template <int CS>
-__device__ __forceinline__ void cluster_arrive() {
-  if constexpr (CS > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
-}
-template <int CS>
-__device__ __forceinline__ void cluster_wait() {
-  if constexpr (CS > 1) asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
-}
-
-// ---- asynchronous DSMEM exchange: st.async stores into another CTA's shared memory, each
-// counted in bytes on an mbarrier of the receiving CTA, which waits for the byte count it
-// expects.  The sender never waits for its stores (no release fence); every wait is bounded.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t mapa_u32(uint32_t local, int rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-  return r;
-}
-
-__device__ __forceinline__ void st_async_f2(uint32_t raddr, float2 v, uint32_t rmbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
-               "f"(v.x), "f"(v.y), "r"(rmbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_expect(uint64_t* bar, uint32_t bytes) {
-  const uint32_t a = smem_u32(bar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-constexpr long kTileSpinLimit = 1L << 22;
-
-// Wait (acquire, cluster scope) for phase 0 of bar; on time-out flag the error and go on.
-__device__ __forceinline__ void mbar_wait_or_flag(uint64_t* bar, int* err) {
-  const uint32_t a = smem_u32(bar);
-  for (long it = 0; it < kTileSpinLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a)
-        : "memory");
-    if (ok) return;
-  }
-  atomicExch(err, 1);
-}
 
 
 // The smoothed normaliser of Eq. 12 (reading A7) at one pixel: omega = d / max(|d|, tau),

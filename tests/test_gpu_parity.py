@@ -7,7 +7,8 @@ Tolerances (relative L2, FP32 CUDA vs FP64 oracle), derived in the design notes:
   * optimiser state after one iteration from the same developed state: 1e-5
     (Psi, P); the moments (mu, v, delta) that carry the per-pixel normalised step
     directly: 2e-3 (v) / 5e-3 (delta);
-  * workload 0 run for 18 iterations from a developed state: Psi, P, O 1e-4;
+  * workload 0 run for 18 iterations from a developed state, and the headline workload's 100: Psi,
+    P, O and every iteration's three cost terms 1e-4;
   * the 20-iteration run from the initial state: twice the FP64 oracle's own spread under
     FP32-sized noise (tests/golden/fp32_spread_w0.json, written by make_fp32_spread.py).
 Sizes: tiny (n=16, one gather tile, ragged LED coverage), single LED, n=32,
@@ -174,7 +175,7 @@ def test_full_run_workload0_matches_oracle():
              L_P=ce[:, 2].max())
     print("w0 run from t=2", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["obj"] < 1e-4
-    assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-3 and e["L_P"] < 1e-3
+    assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-4 and e["L_P"] < 1e-4
 
 
 def test_full_run_degraded_workload_matches_oracle():
@@ -201,7 +202,7 @@ def test_full_run_degraded_workload_matches_oracle():
              L_P=ce[:, 2].max())
     print("w1 100 iterations from t=3", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["obj"] < 1e-4
-    assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-3 and e["L_P"] < 1e-3
+    assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-4 and e["L_P"] < 1e-4
 
 
 def spread(which, model="fp32", at=None):
