@@ -247,7 +247,12 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ELF_CK(cudaEventRecord(h->ev_fork, s0));
     ELF_CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 0);
-    ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi, h->fft_tmp));  // the first pass reads Psi
+    // the branch's kernels chained by programmatic dependent launch only where the branch is the longer
+    // one (N <= 256: 27.3 against 29.5 us per iteration at 64/256/49); beside long tile work the early
+    // CTAs of the high-priority branch would wait on SMs the tile kernels need (0.172 against 0.163 ms
+    // at 256/1024/225)
+    const bool hpdl = h->N <= 256;
+    ELF_CK(launch_fft2(h->ot, h->N, true, h->tw_N, h->aux, psi, h->fft_tmp, false, hpdl));  // the first pass reads Psi
     HessArgs ha{};
     ha.ot = h->ot;
     ha.q = h->q;
@@ -258,8 +263,8 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     ha.tau = (float)h->opt.tau_h;
     ha.eta = (float)h->opt.eta_h;
     ha.iso = h->opt.omega_iso;
-    ELF_CK(launch_hessian(ha, h->aux));
-    ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux, nullptr, h->fft_tmp));
+    ELF_CK(launch_hessian(ha, h->aux, hpdl));
+    ELF_CK(launch_fft2(h->q, h->N, false, h->tw_N, h->aux, nullptr, h->fft_tmp, true, hpdl));  // follows the stencil
     ELF_MARK(h->aux, ELF_STAGE_HESSIAN, 1);
     ELF_CK(cudaEventRecord(h->ev_join, h->aux));
 

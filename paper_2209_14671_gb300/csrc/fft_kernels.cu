@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(FftGrid<L>::ROW_THREADS) fft_rows_kernel(const
   const bool act = row < L;
   float2* g = data + (size_t)(act ? row : 0) * L;
   const float2* gs = src + (size_t)(act ? row : 0) * L;
+  pdl_launch_dependents();
+  pdl_wait();  // the previous kernel of a chain wrote src
   float2 v[P];
   if (act) {
 #pragma unroll
@@ -98,8 +100,10 @@ __global__ void __launch_bounds__(FftGrid<L>::COL_THREADS) fft_cols_kernel(float
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* cols = tw + L;
   const int tid = threadIdx.x;
+  pdl_launch_dependents();
   for (int i = tid; i < L; i += NT) tw[i] = twg[i];
   const int c0 = blockIdx.x * CW;
+  pdl_wait();  // the rows pass wrote data
   // asynchronous 8-byte copies, all in flight at once (CW divides L, so c0 + c < L)
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(cols);
   for (int i = tid; i < CW * L; i += NT) {
@@ -129,6 +133,8 @@ __global__ void __launch_bounds__(128) fft_cols_a_kernel(const float2* __restric
   constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int n2 = blockIdx.y * 4 + threadIdx.y;
+  pdl_launch_dependents();
+  pdl_wait();  // the rows pass wrote data
   float2 v[P];
 #pragma unroll
   for (int n1 = 0; n1 < P; ++n1) v[n1] = data[(size_t)(Q * n1 + n2) * L + x];
@@ -146,6 +152,8 @@ __global__ void __launch_bounds__(128) fft_cols_b_kernel(const float2* __restric
   constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int k1 = blockIdx.y * 4 + threadIdx.y;
+  pdl_launch_dependents();
+  pdl_wait();  // pass A wrote tmp (and read data, which this pass overwrites)
   float2 v[Q];
 #pragma unroll
   for (int n2 = 0; n2 < Q; ++n2) v[n2] = tmp[(size_t)(n2 * P + k1) * L + x];
@@ -154,20 +162,43 @@ __global__ void __launch_bounds__(128) fft_cols_b_kernel(const float2* __restric
   for (int k2 = 0; k2 < Q; ++k2) data[(size_t)(k1 + P * k2) * L + x] = v[k2];
 }
 
+// With pdl, the column pass (and the rows pass when `dep`: it follows another kernel of the stream)
+// starts early by programmatic dependent launch and waits for its predecessor inside.
+template <typename... P, typename... A>
+static cudaError_t launch_maybe_dependent(bool pdl, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                          A... args) {
+  if (pdl) return launch_dependent(k, grid, block, smem, s, args...);
+  k<<<grid, block, smem, s>>>(args...);
+  return cudaGetLastError();
+}
+
 template <int L, bool INV>
-static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src, float2* tmp) {
+static cudaError_t fft2_t(float2* data, const float2* tw, cudaStream_t s, const float2* src, float2* tmp, bool dep,
+                          bool pdl) {
   using G = FftGrid<L>;
-  fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(src ? src : data, data, tw);
+  const float2* in = src ? src : data;
+  cudaError_t e;
+  if (dep && pdl) {
+    e = launch_dependent(fft_rows_kernel<L, INV>, dim3((L + G::RPC - 1) / G::RPC), dim3(G::ROW_THREADS), G::ROW_SMEM, s,
+                         in, data, tw);
+  } else {
+    fft_rows_kernel<L, INV><<<(L + G::RPC - 1) / G::RPC, G::ROW_THREADS, G::ROW_SMEM, s>>>(in, data, tw);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
   if constexpr (L >= 512) {  // at 256 the strip kernel's one launch is faster (64/256/49: 28.5 vs 29.1 us)
     if (tmp) {
       constexpr int P = FftTeam<L>::P, Q = FftTeam<L>::Q;
-      fft_cols_a_kernel<L, INV><<<dim3(L / 32, Q / 4), dim3(32, 4), 0, s>>>(data, tmp, tw);
-      fft_cols_b_kernel<L, INV><<<dim3(L / 32, P / 4), dim3(32, 4), 0, s>>>(tmp, data);
-      return cudaGetLastError();
+      const float2* d = data;
+      const float2* t = tmp;
+      e = launch_maybe_dependent(pdl, fft_cols_a_kernel<L, INV>, dim3(L / 32, Q / 4), dim3(32, 4), 0, s, d, tmp, tw);
+      if (e == cudaSuccess)
+        e = launch_maybe_dependent(pdl, fft_cols_b_kernel<L, INV>, dim3(L / 32, P / 4), dim3(32, 4), 0, s, t, data);
+      return e;
     }
   }
-  fft_cols_kernel<L, INV><<<(L + G::CPC - 1) / G::CPC, G::COL_THREADS, G::COL_SMEM, s>>>(data, tw);
-  return cudaGetLastError();
+  return launch_maybe_dependent(pdl, fft_cols_kernel<L, INV>, dim3((L + G::CPC - 1) / G::CPC), dim3(G::COL_THREADS),
+                                G::COL_SMEM, s, data, tw);
 }
 
 template <int L, bool INV>
@@ -201,10 +232,11 @@ cudaError_t prepare_fft(int L) {
 }
 
 cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s, const float2* src,
-                        float2* tmp) {
-#define ELF_FFT_CASE(LL)                                                     \
-  case LL:                                                                   \
-    return inverse ? fft2_t<LL, true>(data, tw, s, src, tmp) : fft2_t<LL, false>(data, tw, s, src, tmp);
+                        float2* tmp, bool dep, bool pdl) {
+#define ELF_FFT_CASE(LL)                                                        \
+  case LL:                                                                      \
+    return inverse ? fft2_t<LL, true>(data, tw, s, src, tmp, dep, pdl)          \
+                   : fft2_t<LL, false>(data, tw, s, src, tmp, dep, pdl);
   switch (L) {
     ELF_FFT_CASE(16)
     ELF_FFT_CASE(32)

@@ -7,6 +7,32 @@
 
 namespace elf {
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// A chain of kernels on one stream: each kernel lets the next be launched once all its CTAs have
+// started (pdl_launch_dependents), so that the next kernel's CTAs take the SMs it frees and run their
+// independent prologue; the next kernel waits (pdl_wait) for its completion, with its memory visible,
+// before reading what it wrote.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch of a kernel that may start while the previous kernel of the stream still runs (it calls
+// pdl_wait before reading that kernel's results).  The previous operation on the stream must be a
+// kernel launch (no event in between).
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 constexpr int kGatherSeg = 64;    // row segment of the gather lists (two pixels per thread)
 inline int gather_seg(int N) { return N < kGatherSeg ? N : kGatherSeg; }
 constexpr int kCostRing = 4096;   // iterations kept in the cost ring buffer
@@ -101,8 +127,10 @@ cudaError_t prepare_fft(int L);               // sets kernel attributes; call ou
 // src != null: the input is read from src and the result written to data (src is not modified).
 // tmp != null (an L x L scratch array, L >= 512): the column transform runs as the two register passes
 // of the four-step split instead of the shared-memory strip kernel.
+// pdl: the passes are chained by programmatic dependent launch (dep: the rows pass too, which then
+// directly follows another kernel of the stream).
 cudaError_t launch_fft2(float2* data, int L, bool inverse, const float2* tw, cudaStream_t s,
-                        const float2* src = nullptr, float2* tmp = nullptr);
+                        const float2* src = nullptr, float2* tmp = nullptr, bool dep = false, bool pdl = true);
 // dst[y][x] = (-1)^(x+y) * scale * src[y][x] over an L x L array (src may equal dst).
 cudaError_t launch_sign_scale(const float2* src, float2* dst, int L, float scale, cudaStream_t s);
 
@@ -117,7 +145,8 @@ struct HessArgs {
   int iso;
 };
 int hess_blocks(int N);
-cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s);
+// pdl: launched as a programmatic dependent of the column pass it follows on the stream.
+cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s, bool pdl);
 
 // ---------------------------------------------------------------- gather + AdaBelief
 struct GatherArgs {

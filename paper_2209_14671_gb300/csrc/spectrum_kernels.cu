@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
   const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
+  pdl_launch_dependents();
+  pdl_wait();  // the column pass wrote ot
 
   // O = (-1)^(x+y) Ot / A; amplitude and phase (atan2, reading A12)
   for (int i = tid; i < HA * HA; i += 256) {
@@ -253,6 +255,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) hessian_walk_kernel(const Hes
   const bool own = lane >= 2 && lane < 2 + kWalkOut && x < N;
   const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
   float ca = 0.f, cp = 0.f;
+  pdl_launch_dependents();
+  pdl_wait();  // the column pass wrote ot
   // windows: a / phi of rows y, y + 1, y + 2 (A0, A1, A2), omega of rows y - 1, y, y + 1 (W*0, W*1, W*2),
   // O of rows y, y + 1, y + 2
   WalkAP A0, A1, A2, Am;
@@ -327,14 +331,17 @@ int hess_blocks(int N) {
   return walk_cols(N) * ((N + r - 1) / r);
 }
 
-cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s) {
+cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s, bool pdl) {
   const int r = walk_rows(a.N);
   if (r == 0) {
     const int t = (a.N + HT - 1) / HT;
+    if (pdl) return launch_dependent(hessian_kernel, dim3(t, t), dim3(32, 8), 0, s, a);
     hessian_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(a);
   } else if (r == 8) {
+    if (pdl) return launch_dependent(hessian_walk_kernel<8>, dim3(walk_cols(a.N), (a.N + 7) / 8), dim3(32 * kWalkWarps), 0, s, a);
     hessian_walk_kernel<8><<<dim3(walk_cols(a.N), (a.N + 7) / 8), 32 * kWalkWarps, 0, s>>>(a);
   } else {
+    if (pdl) return launch_dependent(hessian_walk_kernel<16>, dim3(walk_cols(a.N), (a.N + 15) / 16), dim3(32 * kWalkWarps), 0, s, a);
     hessian_walk_kernel<16><<<dim3(walk_cols(a.N), (a.N + 15) / 16), 32 * kWalkWarps, 0, s>>>(a);
   }
   return cudaGetLastError();

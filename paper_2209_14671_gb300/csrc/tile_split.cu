@@ -59,6 +59,7 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_inv_kernel(const TileArgs a,
   constexpr int TL = T::TL, NTEAM = kRowThreads / TL, RP = T::PADDED, PL = T::P, Q = T::Q;
   __shared__ __align__(16) float2 tw[NL];
   __shared__ __align__(16) float2 rows[NTEAM * RP];
+  pdl_launch_dependents();
   const int tid = threadIdx.x, lane = tid % TL, team = tid / TL;
   for (int i = tid; i < NL; i += kRowThreads) tw[i] = a.tw[i];
   const int nb = a.nb, nl = a.nled > 0 ? a.nled : a.K;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_fwd_kernel(const TileArgs a,
   const int g = blockIdx.x * NTEAM + team;
   const bool act = g < nl * nb;
   const int li = act ? g / nb : 0, b = act ? g % nb : 0;
+  pdl_wait();  // band_out of the column kernel
   float2 v[PL];
   if (act) {
     const float2* src = band + ((size_t)li * nb + b) * NL;
@@ -182,17 +185,10 @@ __global__ void __launch_bounds__(SplitCfg<NL>::NT, SplitCfg<NL>::MINB)
   const int nb = a.nb, Blo = a.Blo;
   const size_t img = (size_t)led * NL * NL;
 
-  // group 0: twiddles and the band columns of the strip (+ halo); group 1: the measured values
+  pdl_launch_dependents();
+  // group 0: twiddles and the measured values (independent of the inverse row kernel, issued before
+  // waiting for it); group 1: the band columns of the strip (+ halo) it wrote
   for (int i = tid; i < NL / 2; i += NT) cp_async16(tw + 2 * i, a.tw + 2 * i);
-  {
-    const float2* src = band_in + (size_t)li * nb * NL;
-    for (int i = tid; i < nb * WC; i += NT) {
-      const int b = i / WC, c = i - b * WC;
-      const int x = x0 - 1 + c;
-      if (x >= 0 && x < NL) cp_async8(OC + FftTeam<NL>::pidx(Blo + b) * PO + c, src + (size_t)b * NL + x);
-    }
-  }
-  cp_commit();
   {
     constexpr int CH = CW / 4;  // 16-byte chunks per row
     for (int i = tid; i < NL * CH; i += NT) {
@@ -206,7 +202,17 @@ __global__ void __launch_bounds__(SplitCfg<NL>::NT, SplitCfg<NL>::MINB)
     }
   }
   cp_commit();
-  cp_wait<1>();
+  pdl_wait();  // band_in of the inverse row kernel
+  {
+    const float2* src = band_in + (size_t)li * nb * NL;
+    for (int i = tid; i < nb * WC; i += NT) {
+      const int b = i / WC, c = i - b * WC;
+      const int x = x0 - 1 + c;
+      if (x >= 0 && x < NL) cp_async8(OC + FftTeam<NL>::pidx(Blo + b) * PO + c, src + (size_t)b * NL + x);
+    }
+  }
+  cp_commit();
+  cp_wait<0>();
   __syncthreads();
 
   // inverse column transforms of the owned and halo columns (band rows only are non-zero)
@@ -216,7 +222,6 @@ __global__ void __launch_bounds__(SplitCfg<NL>::NT, SplitCfg<NL>::MINB)
     const bool act = (lc < WC) && x >= 0 && x < NL;
     team_fft<NL, true, PO>(OC + (act ? lc : 0), tw, lane, act, Blo, nb);
   }
-  cp_wait<0>();
   __syncthreads();
 
   // o~ = scale * IDFT without the (-1)^(x+y) factor: |o~| = |o| and (-1)^(x+y) o w = o~ w
@@ -395,15 +400,20 @@ cudaError_t launch_split_t(const TileArgs& a, float2* band_in, float2* band_out,
   const size_t smem = cols_smem_bytes<NL>();
   const dim3 grid(nl * (NL / CW));
   const int fid = (a.fidelity >= 2) ? 2 : a.fidelity;
+  const float2* bin = band_in;
+  cudaError_t e;
   switch (2 * fid + (a.iso ? 1 : 0)) {
-    case 0: cols_kernel<NL, 0, 0><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
-    case 1: cols_kernel<NL, 0, 1><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
-    case 2: cols_kernel<NL, 1, 0><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
-    case 3: cols_kernel<NL, 1, 1><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
-    case 4: cols_kernel<NL, 2, 0><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
-    default: cols_kernel<NL, 2, 1><<<grid, NT, smem, s>>>(a, band_in, band_out); break;
+    case 0: e = launch_dependent(cols_kernel<NL, 0, 0>, grid, dim3(NT), smem, s, a, bin, band_out); break;
+    case 1: e = launch_dependent(cols_kernel<NL, 0, 1>, grid, dim3(NT), smem, s, a, bin, band_out); break;
+    case 2: e = launch_dependent(cols_kernel<NL, 1, 0>, grid, dim3(NT), smem, s, a, bin, band_out); break;
+    case 3: e = launch_dependent(cols_kernel<NL, 1, 1>, grid, dim3(NT), smem, s, a, bin, band_out); break;
+    case 4: e = launch_dependent(cols_kernel<NL, 2, 0>, grid, dim3(NT), smem, s, a, bin, band_out); break;
+    default: e = launch_dependent(cols_kernel<NL, 2, 1>, grid, dim3(NT), smem, s, a, bin, band_out); break;
   }
-  rows_fwd_kernel<NL><<<(rows + NTEAM - 1) / NTEAM, kRowThreads, 0, s>>>(a, band_out);
+  if (e != cudaSuccess) return e;
+  const float2* bout = band_out;
+  e = launch_dependent(rows_fwd_kernel<NL>, dim3((rows + NTEAM - 1) / NTEAM), dim3(kRowThreads), 0, s, a, bout);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
