@@ -34,33 +34,35 @@ __device__ __forceinline__ double block_sum_double(double v, double* red) {
 }
 
 // Smoothed L1 of a 3-vector (reading A7): cost and omega = h / max(|h|, tau)
-// (isotropic), or the same rule per component (anisotropic).
-__device__ __forceinline__ float huber3(float& h0, float& h1, float& h2, float tau, int iso) {
+// (isotropic), or the same rule per component (anisotropic).  hit = 1 / (2 tau) (0 when tau = 0,
+// where the quadratic branch is never taken), hoisted out of the per-pixel work.
+__device__ __forceinline__ float huber3(float& h0, float& h1, float& h2, float tau, float hit, int iso) {
   if (iso) {
     const float ss = h0 * h0 + h1 * h1 + h2 * h2;
     const float inv = rsqrtf(fmaxf(ss, fmaxf(tau * tau, 1e-36f)));
     h0 *= inv;
     h1 *= inv;
     h2 *= inv;
-    return (ss >= tau * tau) ? ss * inv : ss / (2.f * tau) + 0.5f * tau;
+    return (ss >= tau * tau) ? ss * inv : ss * hit + 0.5f * tau;
   }
   float c = 0.f;
   float* hs[3] = {&h0, &h1, &h2};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float a = fabsf(*hs[i]);
-    c += (a >= tau) ? a : a * a / (2.f * tau) + 0.5f * tau;
+    c += (a >= tau) ? a : a * a * hit + 0.5f * tau;
     *hs[i] /= fmaxf(a, fmaxf(tau, 1e-18f));  // 0 at the origin when tau = 0
   }
   return c;
 }
 
 // ------------------------------------------------------------------ Hessian (Eqs. 6-7, 13-14)
-constexpr int HT = 32;            // output tile side
+constexpr int HT = 16;            // output tile side (16 x 16 blocks: 64/256/49 at 24.7 against 27.0 us per
+                                  // iteration with 32 x 32 tiles and 32 x 8 blocks)
 constexpr int HA = HT + 4;        // amplitude/phase tile with a 2-pixel halo
 constexpr int HW = HT + 2;        // omega tile with a 1-pixel halo
 
-// Block of 32 x 8 threads per 32 x 32 output tile (2-pixel halo).
+// Block of HT x (256 / HT) threads per HT x HT output tile (2-pixel halo).
 __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   __shared__ float s_a[HA][HA + 1];
   __shared__ float s_p[HA][HA + 1];
@@ -69,8 +71,9 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   const int N = a.N;
   const int tx0 = blockIdx.x * HT, ty0 = blockIdx.y * HT;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * 32 + tx;
+  const int tid = ty * HT + tx;
   const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
+  const float hit = a.tau > 0.f ? 0.5f / a.tau : 0.f;
   pdl_launch_dependents();
   pdl_wait();  // the column pass wrote ot
 
@@ -108,11 +111,11 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
         float h0 = s_a[cy][cx - 1] - 2.f * s_a[cy][cx] + s_a[cy][cx + 1];
         float h1 = s_a[cy - 1][cx] - 2.f * s_a[cy][cx] + s_a[cy + 1][cx];
         float h2 = r2 * 0.25f * (s_a[cy + 1][cx + 1] - s_a[cy + 1][cx - 1] - s_a[cy - 1][cx + 1] + s_a[cy - 1][cx - 1]);
-        const float fa = huber3(h0, h1, h2, a.tau, a.iso);
+        const float fa = huber3(h0, h1, h2, a.tau, hit, a.iso);
         float g0 = s_p[cy][cx - 1] - 2.f * s_p[cy][cx] + s_p[cy][cx + 1];
         float g1 = s_p[cy - 1][cx] - 2.f * s_p[cy][cx] + s_p[cy + 1][cx];
         float g2 = r2 * 0.25f * (s_p[cy + 1][cx + 1] - s_p[cy + 1][cx - 1] - s_p[cy - 1][cx + 1] + s_p[cy - 1][cx - 1]);
-        const float fp = huber3(g0, g1, g2, a.tau, a.iso);
+        const float fp = huber3(g0, g1, g2, a.tau, hit, a.iso);
         w[0] = h0; w[1] = h1; w[2] = h2; w[3] = g0; w[4] = g1; w[5] = g2;
         if (ly >= 1 && ly <= HT && lx >= 1 && lx <= HT) {  // owned pixel
           ca += fa;
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(256) hessian_kernel(const HessArgs a) {
   __syncthreads();
 
   // q = alpha O/(2 max(a,eta)) H^T omega_a + beta (i/2) O/(a^2+eta) H^T omega_phi
-  for (int ly = ty; ly < HT; ly += 8) {
+  for (int ly = ty; ly < HT; ly += 256 / HT) {
     const int lx = tx;
     const int y = ty0 + ly, x = tx0 + lx;
     if (y >= N || x >= N) continue;
@@ -203,7 +206,7 @@ __device__ __forceinline__ void walk_ap(const HessArgs& a, int x, int r, WalkAP&
 
 // omega of row r (rows r - 1, r, r + 1 of a and phi given) for both fields; the smoothed cost of the
 // pixel is added when count is set.  Zero outside the interior.
-__device__ __forceinline__ void walk_omega(const HessArgs& a, bool inside, bool count, const WalkAP& u,
+__device__ __forceinline__ void walk_omega(const HessArgs& a, float hit, bool inside, bool count, const WalkAP& u,
                                            const WalkAP& m, const WalkAP& d, WalkW& wa, WalkW& wp, float& ca,
                                            float& cp) {
   const float r2 = 1.41421356237309505f;
@@ -212,11 +215,11 @@ __device__ __forceinline__ void walk_omega(const HessArgs& a, bool inside, bool 
     h0 = m.aL - 2.f * m.aM + m.aR;
     h1 = u.aM - 2.f * m.aM + d.aM;
     h2 = r2 * 0.25f * (d.aR - d.aL - u.aR + u.aL);
-    const float fa = huber3(h0, h1, h2, a.tau, a.iso);
+    const float fa = huber3(h0, h1, h2, a.tau, hit, a.iso);
     g0 = m.pL - 2.f * m.pM + m.pR;
     g1 = u.pM - 2.f * m.pM + d.pM;
     g2 = r2 * 0.25f * (d.pR - d.pL - u.pR + u.pL);
-    const float fp = huber3(g0, g1, g2, a.tau, a.iso);
+    const float fp = huber3(g0, g1, g2, a.tau, hit, a.iso);
     if (count) {
       ca += fa;
       cp += fp;
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) hessian_walk_kernel(const Hes
   const bool own = lane >= 2 && lane < 2 + kWalkOut && x < N;
   const float alpha = (float)a.weights[0], beta = (float)a.weights[1];
   float ca = 0.f, cp = 0.f;
+  const float hit = a.tau > 0.f ? 0.5f / a.tau : 0.f;
   pdl_launch_dependents();
   pdl_wait();  // the column pass wrote ot
   // windows: a / phi of rows y, y + 1, y + 2 (A0, A1, A2), omega of rows y - 1, y, y + 1 (W*0, W*1, W*2),
@@ -268,9 +272,9 @@ __global__ void __launch_bounds__(32 * kWalkWarps) hessian_walk_kernel(const Hes
   WalkW Wa0, Wa1, Wa2, Wp0, Wp1, Wp2;
   {
     const int r = y0 - 1;
-    walk_omega(a, xint && r >= 1 && r <= N - 2, false, Am, A0, A1, Wa1, Wp1, ca, cp);
+    walk_omega(a, hit, xint && r >= 1 && r <= N - 2, false, Am, A0, A1, Wa1, Wp1, ca, cp);
     const int r1 = y0;
-    walk_omega(a, xint && r1 >= 1 && r1 <= N - 2, own && r1 < N, A0, A1, A2, Wa2, Wp2, ca, cp);
+    walk_omega(a, hit, xint && r1 >= 1 && r1 <= N - 2, own && r1 < N, A0, A1, A2, Wa2, Wp2, ca, cp);
   }
   // shift: a / phi rows y0 .. y0 + 1 into A0 .. A1, O likewise
   A0 = A1;
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) hessian_walk_kernel(const Hes
     Wa1 = Wa2;
     Wp1 = Wp2;
     const int r = y + 1;
-    walk_omega(a, xint && r >= 1 && r <= N - 2, own && i + 1 < ROWS && r < N, A0, A1, A2, Wa2, Wp2, ca, cp);
+    walk_omega(a, hit, xint && r >= 1 && r <= N - 2, own && i + 1 < ROWS && r < N, A0, A1, A2, Wa2, Wp2, ca, cp);
     // q of row y: alpha O / (2 max(a, eta)) H^T omega_a + beta (i/2) O / (a^2 + eta) H^T omega_phi,
     // times (-1)^(x+y) / A for the forward transform
     if (own && y < N) {
@@ -320,8 +324,9 @@ static int walk_cols(int N) { return (((N + kWalkOut - 1) / kWalkOut) + kWalkWar
 
 // Which kernel runs, measured on GB300 in the whole iteration: the tiled kernel at N <= 256 (64/256/49:
 // 29.5 against 30.8 us), the walk with 8-row strips at N = 512 (52.7 against 53.4 us at 128/512/225)
-// and with 16-row strips from N = 1024 (161.0 against 163.0 us at 256/1024/225).  Shorter strips give
-// more warps for latency hiding and cost recomputed halo rows.
+// and with 16-row strips from N = 1024 (161.0 against 163.0 us at 256/1024/225; 32-row strips shorten
+// the tile stage but end the branch later: 0.168 against 0.164 ms per step).  Shorter strips give more
+// warps for latency hiding and cost recomputed halo rows.
 static int walk_rows(int N) { return N <= 256 ? 0 : (N <= 512 ? 8 : 16); }
 
 // Blocks of the launch, each writing one (L_A, L_Phi) cost pair.
@@ -335,8 +340,8 @@ cudaError_t launch_hessian(const HessArgs& a, cudaStream_t s, bool pdl) {
   const int r = walk_rows(a.N);
   if (r == 0) {
     const int t = (a.N + HT - 1) / HT;
-    if (pdl) return launch_dependent(hessian_kernel, dim3(t, t), dim3(32, 8), 0, s, a);
-    hessian_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(a);
+    if (pdl) return launch_dependent(hessian_kernel, dim3(t, t), dim3(HT, 256 / HT), 0, s, a);
+    hessian_kernel<<<dim3(t, t), dim3(HT, 256 / HT), 0, s>>>(a);
   } else if (r == 8) {
     if (pdl) return launch_dependent(hessian_walk_kernel<8>, dim3(walk_cols(a.N), (a.N + 7) / 8), dim3(32 * kWalkWarps), 0, s, a);
     hessian_walk_kernel<8><<<dim3(walk_cols(a.N), (a.N + 7) / 8), 32 * kWalkWarps, 0, s>>>(a);
