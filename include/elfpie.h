@@ -169,6 +169,19 @@ int elf_get_spectrum(elf_handle h, float* psi, int is_device);
  * each iteration started from, oldest first, for the last min(t, max_iter, 4096)
  * iterations, into out [count][3] (host).  Returns count (>= 0) or an error. */
 int elf_get_costs(elf_handle h, double* out, int max_iter);
+/* Per-iteration FP64 norms (||g||, ||Delta Psi||) of the Psi update of Eq. 19: g = dL/dconj(Psi) of
+ * Eq. 8 (Eq. 9 plus Eqs. 13-15) at the state the iteration started from, Delta Psi = Psi^(t+1) - Psi^t,
+ * both summed over the N x N spectrum in a fixed order.  Oldest first, for the last min(t, max_iter,
+ * 4096) iterations (t counts iterations since elf_set_measurements, or from the t of elf_set_state),
+ * into out [count][2] (host).  Returns count (>= 0) or an error (ELF_ENUMERIC for a non-finite norm). */
+int elf_get_norms(elf_handle h, double* out, int max_iter);
+/* Self-test of the failure path of the library's bounded device waits (the tile kernels' cluster
+ * exchanges wait on mbarriers with a poll limit; a wait that runs out sets the handle's error flag,
+ * after which the getters return ELF_ETIMEOUT).  Runs one warp that waits on a barrier phase nothing
+ * completes, with `limit` polls (1 .. 2^30), on the handle's stream: the wait runs out, sets the flag
+ * and the kernel returns, leaving the device usable.  The handle then reports ELF_ETIMEOUT from its
+ * getters for good (destroy it).  *ms (may be null) gets the kernel's duration. */
+int elf_selftest_wait_timeout(elf_handle h, long long limit, double* ms);
 /* Copies the optimiser state out / in (checkpoint and resume). */
 int elf_get_state(elf_handle h, const elf_state* out, int is_device);
 int elf_set_state(elf_handle h, const elf_state* in, int is_device);
@@ -284,6 +297,11 @@ int elf_server_progress(elf_server s, long long* done_tags, int max_done, int* n
 /* Copies a finished request's object O [N][N][2] float to host memory and
  * forgets the request.  ELF_ESTATE if it has not finished. */
 int elf_server_result(elf_server s, long long tag, float* obj);
+/* Withdraws a request: a queued one is dropped; a running one (its whole job is already on the
+ * device, which cannot be interrupted) is waited for, its handle kept for reuse and its result
+ * discarded; a finished, uncollected one has its result discarded.  On return the request's input
+ * buffer is no longer used and its tag is free.  ELF_EINVAL for an unknown tag. */
+int elf_server_cancel(elf_server s, long long tag);
 /* Device bytes held, jobs in flight, requests waiting, handles created so far. */
 int elf_server_stats(elf_server s, size_t* used_bytes, int* n_active, int* n_queued, int* n_created);
 /* Waits for jobs in flight, then frees everything. */

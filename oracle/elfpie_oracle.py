@@ -41,7 +41,8 @@ Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
 (brute-force DFT, Parseval, adjoint identities, central differences along 32
 seeded directions with a scanned step, affine null space of H, closed forms for
 alpha and the first AdaBelief step, the pupil update of ``iteration`` against a
-hand-summed filter and the closed-form first step, noiseless convergence).  The reconstruction-quality numbers of the paper's Tables 2-4 are
+hand-summed filter and the closed-form first step, the update norms against the first step's
+closed form and the returned states, noiseless convergence).  The reconstruction-quality numbers of the paper's Tables 2-4 are
 parity unpinned (their images and comparison codes are not available).
 """
 from __future__ import annotations
@@ -56,7 +57,7 @@ __all__ = [
     "crop", "crop_adjoint", "forward_field", "forward_intensity",
     "grad_op", "grad_adj", "huber", "hessian_op", "hessian_adj",
     "fidelity_cost_grad", "object_from_spectrum", "spectrum_from_object",
-    "hessian_cost_grad", "adabelief", "gauss3", "filter3", "alpha_estimate",
+    "hessian_cost_grad", "adabelief", "update_norms", "gauss3", "filter3", "alpha_estimate",
     "scaling_map", "scaling_map_slope",
     "init_state", "iteration", "run", "total_cost", "centre_led",
     "LAPLACE_KERNEL", "gaussian_kernel_periodic", "circular_convolve", "illumination_pattern",
@@ -545,7 +546,13 @@ def init_state(I, geo: Geometry, k_xy, opt: Options) -> State:
         t=0, alpha=float(alpha), beta=float(beta))
 
 
-def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity=None):
+def update_norms(g_psi, step):
+    """(||g||, ||Delta Psi||) of one Psi update: the Euclidean norms over the N x N spectrum of
+    the gradient used by Eq. 19 and of Psi^(t+1) - Psi^t = -Delta."""
+    return float(np.sqrt(np.sum(np.abs(g_psi) ** 2))), float(np.sqrt(np.sum(np.abs(step) ** 2)))
+
+
+def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity=None, norms=None):
     """One outer iteration of Algorithm 1 from state t to t+1.
 
     Gradients are evaluated at (Psi^t, P^t) (Sec. 3.3-3.4), then Psi and P are
@@ -553,6 +560,7 @@ def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity
     ``fidelity``, if given, replaces the call of fidelity_cost_grad (same
     arguments and results); oracle/parallel.py passes one that splits the LED
     sum over processes.  It is started before the Hessian branch is evaluated.
+    ``norms``, if a list, gets the iteration's update_norms appended.
     Returns (new_state, costs=(L_fid, L_A, L_Phi) at state t, extras or None).
     """
     if fidelity is None:
@@ -567,8 +575,10 @@ def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity
     t = state.t + 1
     s = state.copy()
     s.t = t
-    s.psi, s.mu_psi, s.v_psi, s.delta_psi, _ = adabelief(
+    s.psi, s.mu_psi, s.v_psi, s.delta_psi, step = adabelief(
         state.psi, g_psi, state.mu_psi, state.v_psi, state.delta_psi, t, opt)
+    if norms is not None:
+        norms.append(update_norms(g_psi, step))
     if opt.learn_pupil:
         p_base = filter3(state.pupil) if opt.pupil_filter else state.pupil
         p_new, s.mu_p, s.v_p, s.delta_p, _ = adabelief(

@@ -38,12 +38,12 @@ __device__ __forceinline__ void mbar_init_expect(uint64_t* bar, uint32_t bytes) 
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
 
-constexpr long kTileSpinLimit = 1L << 22;
+constexpr long kTileSpinLimit = 1L << 18;  // about 1 s of polls on GB300 (3.8 us per poll, measured)
 
-// Wait (acquire, cluster scope) for phase 0 of bar; on time-out flag the error and go on.
-__device__ __forceinline__ void mbar_wait_or_flag(uint64_t* bar, int* err) {
+// Wait (acquire, cluster scope) for phase 0 of bar; after `limit` polls flag the error and go on.
+__device__ __forceinline__ void mbar_wait_or_flag(uint64_t* bar, int* err, long limit = kTileSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long it = 0; it < kTileSpinLimit; ++it) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"

@@ -107,6 +107,9 @@ struct elf_handle_s {
   double *cost_fid = nullptr, *cost_h = nullptr, *ring = nullptr, *weights = nullptr, *alpha_part = nullptr,
          *out4 = nullptr;
   int *t_dev = nullptr, *flag = nullptr;
+  float2* norm_part = nullptr;  // [2 parities][gather blocks] sums of |g|^2 and |Delta|^2
+  double* norm_ring = nullptr;  // [kCostRing][2] (||g||, ||Delta Psi||)
+  int* norm_state = nullptr;    // [0], [1] partials of parity 0 / 1 pending; [2] next ring slot
   size_t device_bytes = 0;  // sum of this handle's device allocations
   // tensor-core tile path (tile_dft = 1)
   unsigned char *tc_iX = nullptr, *tc_iY = nullptr, *tc_iW = nullptr, *tc_iZ = nullptr;  // operand images
@@ -241,6 +244,9 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
   ga.g2 = (float)h->opt.gamma2;
   ga.eta = (float)h->opt.eta_opt;
   ga.mode = mode;
+  const int nblk = gather_blocks(h->N);
+  ga.norm_part = h->norm_part + (size_t)par * nblk;
+  ga.norm_pending = h->norm_state + par;
   if (parts & kPartFront) {
     ELF_MARK(s0, ELF_STAGE_ITERATION, 0);
     // Hessian branch on the auxiliary stream: O, Eqs. 6-7 and 13-14, F_A^H
@@ -380,7 +386,10 @@ int enqueue_iteration(elf_handle h, int mode, cudaStream_t s0, const float2* psi
     // in update mode it also closes the iteration (t, running powers, the next bias corrections)
     ELF_CK(launch_cost_reduce(fid, nfid, h->cost_ff, (tc || mx) ? 0 : h->K * h->cs, h->cost_h,
                               h->hblocks, mode == 0 ? h->ring : nullptr, h->t_dev, mode == 1 ? h->out4 : nullptr,
-                              h->weights, mode == 0 ? bc_next : nullptr, h->gp, h->opt.gamma1, h->opt.gamma2, h->aux));
+                              h->weights, mode == 0 ? bc_next : nullptr, h->gp, h->opt.gamma1, h->opt.gamma2,
+                              NormArgs{h->norm_part + (size_t)(par ^ 1) * nblk, nblk, h->norm_state + (par ^ 1),
+                                       h->norm_state + 2, h->norm_ring},
+                              h->aux));
   }
   ELF_MARK(h->aux, ELF_STAGE_COST, 1);
   ELF_CK(cudaEventRecord(h->ev_cost, h->aux));
@@ -736,6 +745,9 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   if ((rc = dalloc(h, &h->alpha_part, (size_t)alpha_blocks(K, n)))) return rc;
   if ((rc = dalloc(h, &h->out4, 4))) return rc;
   if ((rc = dalloc(h, &h->t_dev, 1))) return rc;
+  if ((rc = dalloc(h, &h->norm_part, (size_t)2 * gather_blocks(N)))) return rc;
+  if ((rc = dalloc(h, &h->norm_ring, (size_t)2 * kCostRing))) return rc;
+  if ((rc = dalloc(h, &h->norm_state, 3))) return rc;
   if ((rc = dalloc(h, &h->flag, 1))) return rc;
   if ((rc = dalloc(h, &h->bc, 4))) return rc;
   if ((rc = dalloc(h, &h->gp, 2))) return rc;
@@ -763,6 +775,8 @@ static int create_impl(const elf_problem* p, const elf_options* o, void* stream,
   ELF_CK(prepare_fft(N));
   ELF_CK(launch_support_pupil(h->pupil_unit, h->sidx_map, n, h->user));
   ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), h->user));
+  ELF_CK(cudaMemsetAsync(h->norm_state, 0, 3 * sizeof(int), h->user));
+  ELF_CK(cudaMemsetAsync(h->norm_ring, 0, 2 * kCostRing * sizeof(double), h->user));
   ELF_CK(cudaMemsetAsync(h->ring, 0, 3 * kCostRing * sizeof(double), h->user));
   ELF_CK(cudaStreamSynchronize(h->user));
   return ELF_OK;
@@ -811,6 +825,7 @@ int init_state_async(elf_handle h) {
   ELF_CK(launch_fill_f(h->v_p, B, 0.f, s));
   ELF_CK(launch_fill_f(h->delta_p, B, (float)(h->opt.s0_pupil * h->opt.s0_pupil), s));
   ELF_CK(cudaMemsetAsync(h->t_dev, 0, sizeof(int), s));
+  ELF_CK(cudaMemsetAsync(h->norm_state, 0, 3 * sizeof(int), s));
   ELF_CK(launch_init_bias(h->bc + 2 * h->cur, h->gp, h->opt.gamma1, h->opt.gamma2, s));
   h->have_meas = true;
   return ELF_OK;
@@ -1013,6 +1028,51 @@ int elf_get_costs(elf_handle h, double* out, int max_iter) {
   return count;
 }
 
+int elf_selftest_wait_timeout(elf_handle h, long long limit, double* ms) {
+  if (int rc = check(h)) return rc;
+  if (limit < 1 || limit > (1LL << 30)) return set_error(ELF_EINVAL, "limit must be in [1, 2^30]");
+  cudaEvent_t a = nullptr, b = nullptr;
+  ELF_CK(cudaEventCreate(&a));
+  cudaError_t e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, h->user);
+  if (e == cudaSuccess) e = launch_wait_timeout(h->tc_err, limit, h->user);
+  if (e == cudaSuccess) e = cudaEventRecord(b, h->user);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return set_error(ELF_ECUDA, cudaGetErrorString(e));
+  if (ms) *ms = t;
+  return ELF_OK;
+}
+
+int elf_get_norms(elf_handle h, double* out, int max_iter) {
+  if (int rc = check(h)) return rc;
+  if (!out || max_iter < 0) return set_error(ELF_EINVAL, "bad output");
+  // the most recent update's norms, if no later cost reduction has added them up yet
+  const int nblk = gather_blocks(h->N);
+  for (int p = 0; p < 2; ++p)
+    ELF_CK(launch_norms_finalize(NormArgs{h->norm_part + (size_t)p * nblk, nblk, h->norm_state + p, h->norm_state + 2,
+                                          h->norm_ring},
+                                 h->user));
+  int ns[3] = {0, 0, 0};
+  ELF_CK(cudaMemcpyAsync(ns, h->norm_state, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->user));
+  ELF_CK(cudaStreamSynchronize(h->user));
+  const int t = ns[2];
+  int count = t < max_iter ? t : max_iter;
+  if (count > kCostRing) count = kCostRing;
+  std::vector<double> ring(2 * kCostRing);
+  ELF_CK(cudaMemcpy(ring.data(), h->norm_ring, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < count; ++i) {
+    const int it = t - count + i;
+    std::memcpy(out + 2 * i, ring.data() + 2 * (it % kCostRing), 2 * sizeof(double));
+  }
+  for (int i = 0; i < 2 * count; ++i)
+    if (!std::isfinite(out[i])) return set_error(ELF_ENUMERIC, "non-finite norm");
+  return count;
+}
+
 int elf_get_state(elf_handle h, const elf_state* st, int is_device) {
   if (int rc = check(h)) return rc;
   if (!st) return set_error(ELF_EINVAL, "null state");
@@ -1063,6 +1123,8 @@ int elf_set_state(elf_handle h, const elf_state* st, int is_device) {
   const int t = st->t;
   const double w[2] = {st->alpha, st->beta};
   ELF_CK(cudaMemcpyAsync(h->t_dev, &t, sizeof(int), cudaMemcpyHostToDevice, s));
+  const int ns[3] = {0, 0, t};  // nothing pending; the norm ring continues at the state's iteration count
+  ELF_CK(cudaMemcpyAsync(h->norm_state, ns, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
   ELF_CK(cudaMemcpyAsync(h->weights, w, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
   if (int rc = upload_bias(h, t, s)) return rc;
   ELF_CK(cudaStreamSynchronize(s));

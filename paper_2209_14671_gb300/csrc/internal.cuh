@@ -166,7 +166,24 @@ struct GatherArgs {
   int N, n, S, K, tiles_x;
   float g1, g2, eta;
   int mode;               // 0 = AdaBelief update, 1 = write g
+  // update mode: this block's sums of |g|^2 and |Delta|^2 into norm_part[block] (the buffer of this
+  // iteration's parity, gather_blocks(N) entries), and *norm_pending = 1
+  float2* norm_part;
+  int* norm_pending;
 };
+int gather_blocks(int N);
+// The norms (||g||, ||Delta Psi||) of an update from its gather's partials: part [nblk], added in block
+// order when *pending, into ring [kCostRing][2] at slot *slot % kCostRing; then *slot += 1, *pending = 0.
+struct NormArgs {
+  const float2* part;
+  int nblk;
+  int* pending;
+  int* slot;
+  double* ring;
+};
+cudaError_t launch_norms_finalize(const NormArgs& n, cudaStream_t s);
+// A wait that runs out on purpose (peak.cu): sets *err after `limit` polls of a barrier nothing completes.
+cudaError_t launch_wait_timeout(int* err, long long limit, cudaStream_t s);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- pupil
@@ -194,7 +211,8 @@ cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s);
 // bc_next != null (with ring): also t += 1, gp *= gamma and bc_next = the next iteration's corrections.
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
                                double* ring, int* t_dev, double* out4, const double* weights, float* bc_next,
-                               double* gp, double g1, double g2, cudaStream_t s);
+                               double* gp, double g1, double g2, const NormArgs& nprev,
+                               cudaStream_t s);
 cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaStream_t s);
 int alpha_blocks(int K, int n);
 cudaError_t launch_alpha(const float* I, int K, int n, int amplitude, double* partial, double* weights,

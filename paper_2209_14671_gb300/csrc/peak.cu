@@ -1,3 +1,5 @@
+// Diagnostics of the library on the current GPU.
+//
 // elf_measure_fp32_peak: the FP32 FMA throughput of the current GPU, measured.
 //
 // The tile kernel of Eqs. 1-12 is bound by FP32 arithmetic, so its roofline needs the
@@ -7,11 +9,16 @@
 // 2 FLOP per FMA over the launch's CUDA-event duration.  m and c keep every chain
 // bounded and normal (|x| stays near c / (1 - m)), and the result is stored only under a
 // condition the compiler cannot decide, so no FMA can be removed.
+//
+// launch_wait_timeout (elf_selftest_wait_timeout): one warp waits on an mbarrier phase that nothing
+// completes (it expects 16 bytes that are never sent), with the bounded wait of the tile kernels'
+// exchanges and a caller's poll limit; the wait runs out, sets the error flag and the kernel returns.
 #include <cuda_runtime.h>
 
 #include <string>
 
 #include "../../include/elfpie.h"
+#include "dsmem.cuh"
 
 namespace {
 
@@ -39,7 +46,21 @@ __global__ void __launch_bounds__(kThreads) fma_peak_kernel(float m, float c, in
 
 namespace elf {
 int noalloc_set_error(int code, const char* msg);
+
+namespace {
+__global__ void __launch_bounds__(32) wait_timeout_kernel(int* err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init_expect(&bar, 16);
+  __syncthreads();
+  mbar_wait_or_flag(&bar, err, (long)limit);
 }
+}  // namespace
+
+cudaError_t launch_wait_timeout(int* err, long long limit, cudaStream_t s) {
+  wait_timeout_kernel<<<1, 32, 0, s>>>(err, limit);
+  return cudaGetLastError();
+}
+}  // namespace elf
 
 extern "C" int elf_measure_fp32_peak(int iters, int repeats, void* cuda_stream, double* tflops, double* best_ms) {
   if (!tflops || iters < 1 || repeats < 1) return elf::noalloc_set_error(ELF_EINVAL, "bad arguments");

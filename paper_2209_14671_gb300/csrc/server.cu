@@ -273,6 +273,42 @@ int elf_server_result(elf_server s, long long tag, float* obj) {
   return ELF_OK;
 }
 
+int elf_server_cancel(elf_server s, long long tag) {
+  if (!s) return fail(ELF_EINVAL, "null server");
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if ((*it)->tag != tag) continue;
+    delete *it;
+    s->queue.erase(it);
+    return ELF_OK;
+  }
+  for (size_t i = 0; i < s->active.size(); ++i) {
+    Request* r = s->active[i];
+    if (r->tag != tag) continue;
+    // its whole job is on the device already: wait for it, keep the handle, drop the result
+    const cudaError_t e = cudaEventSynchronize(r->done);
+    if (e != cudaSuccess) return fail(ELF_ECUDA, std::string("request failed: ") + cudaGetErrorString(e));
+    Pooled p;
+    p.h = r->h;
+    p.stream = r->stream;
+    p.bytes = elf::handle_device_bytes(r->h);
+    p.last_use = ++s->clock;
+    s->idle.emplace(r->key, p);
+    s->pinned_free[r->N].push_back(r->result);
+    cudaEventDestroy(r->done);
+    s->active.erase(s->active.begin() + (long)i);
+    delete r;
+    return ELF_OK;
+  }
+  auto it = s->finished.find(tag);
+  if (it == s->finished.end()) return fail(ELF_EINVAL, "unknown tag");
+  Request* r = it->second;
+  s->pinned_free[r->N].push_back(r->result);
+  cudaEventDestroy(r->done);
+  s->finished.erase(it);
+  delete r;
+  return ELF_OK;
+}
+
 int elf_server_stats(elf_server s, size_t* used_bytes, int* n_active, int* n_queued, int* n_created) {
   if (!s) return fail(ELF_EINVAL, "null server");
   if (used_bytes) *used_bytes = s->used;

@@ -457,16 +457,82 @@ __global__ void __launch_bounds__(256, 5) gather_kernel(const GatherArgs a) {
   float2 mua = make_float2(mu.x, mu.y), mub = make_float2(mu.z, mu.w);
   const float2 da = adabelief_step(ga, mua, v.x, dl.x, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
   const float2 db = adabelief_step(gb, mub, v.y, dl.y, a.g1, a.g2, a.eta, a.bc[0], a.bc[1]);
+  const float part[2] = {cabs2(ga) + cabs2(gb), cabs2(da) + cabs2(db)};
   *reinterpret_cast<float4*>(a.psi_out + k) = make_float4(ps.x - da.x, ps.y - da.y, ps.z - db.x, ps.w - db.y);
   *reinterpret_cast<float4*>(a.mu + k) = make_float4(mua.x, mua.y, mub.x, mub.y);
   *reinterpret_cast<float2*>(a.v + k) = v;
   *reinterpret_cast<float2*>(a.delta + k) = dl;
+
+  // ||g|| and ||Delta Psi|| of this iteration: each block's FP32 sums of |g|^2 and |Delta|^2 (a fixed
+  // tree over its 512 positive terms: relative error at most 9 * 2^-24), added in block order with
+  // error-free pair sums by the next cost reduction (norms_finalize)
+  __shared__ float2 red[8];
+  float s0 = part[0], s1 = part[1];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, off);
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) red[tid >> 5] = make_float2(s0, s1);
+  __syncthreads();
+  if (tid == 0) {
+    float2 t = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t = make_float2(t.x + red[w].x, t.y + red[w].y);
+    a.norm_part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    if (blockIdx.x == 0 && blockIdx.y == 0) *a.norm_pending = 1;
+  }
 }
+
+// The norms of an update from its gather's block partials: the blocks in index order (eight loads
+// in flight per thread, then one block sum), square roots into the next ring slot.  One block; every
+// thread calls it.  A no-op when no partials are pending.
+__device__ void norms_finalize(const float2* part, int nblk, int* pending, int* slot, double* ring, float* red) {
+  if (*pending == 0) return;  // the same value for every thread: no kernel beside this one writes it
+  const int tid = threadIdx.x, nt = blockDim.x;
+  FF t[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  constexpr int U = 8;
+  for (int i0 = tid; i0 < nblk; i0 += U * nt) {
+    float2 p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) p[u] = (i0 + u * nt < nblk) ? __ldcg(part + i0 + u * nt) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (i0 + u * nt < nblk) {
+        t[0] = ff_add(t[0], FF{p[u].x, 0.f});
+        t[1] = ff_add(t[1], FF{p[u].y, 0.f});
+      }
+    }
+  }
+  double nrm[2];
+  block_sum_ff<2>(t, red, nrm);
+  if (tid == 0) {
+    const int it = *slot;
+    ring[2 * (it % kCostRing)] = sqrt(nrm[0]);
+    ring[2 * (it % kCostRing) + 1] = sqrt(nrm[1]);
+    *slot = it + 1;
+    *pending = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) norms_finalize_kernel(const float2* part, int nblk, int* pending, int* slot,
+                                                              double* ring) {
+  __shared__ float red[2 * 2 * 8];
+  norms_finalize(part, nblk, pending, slot, ring, red);
+}
+
+cudaError_t launch_norms_finalize(const NormArgs& n, cudaStream_t s) {
+  norms_finalize_kernel<<<1, 256, 0, s>>>(n.part, n.nblk, n.pending, n.slot, n.ring);
+  return cudaGetLastError();
+}
+
+int gather_blocks(int N) { return N * N / 512; }  // 512 pixels per block (see launch_gather)
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
   const int seg = gather_seg(a.N);          // 64, or 32 for a 32 x 32 spectrum
   const dim3 block(seg / 2, 256 / (seg / 2)); // one thread per two pixels of a segment
-  const dim3 grid(a.tiles_x, a.N / block.y);
+  const dim3 grid(a.tiles_x, a.N / block.y);  // gather_blocks(N) blocks in all
   gather_kernel<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -596,7 +662,7 @@ cudaError_t launch_pupil_offsupport(const PupilArgs& a, cudaStream_t s) {
 __global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int nfid, const float2* fidff, int nff,
                                                            const double* hp, int nh, double* ring,
                                                            int* t_dev, double* out4, const double* weights, float* bc_next,
-                                                           double* gp, double g1, double g2) {
+                                                           double* gp, double g1, double g2, const NormArgs nprev) {
   // per-thread sums over a fixed stride (FP64 partials in FP64, (hi, lo) pairs as pairs),
   // then one block sum of (hi, lo) pairs
   __shared__ float red[2 * 3 * 32];
@@ -646,6 +712,9 @@ __global__ void __launch_bounds__(256) cost_reduce_kernel(const double* fid, int
       }
     }
   }
+  // in update mode, the norms of the previous update (its gather has finished: it precedes this
+  // iteration's fork)
+  if (bc_next && nprev.part) norms_finalize(nprev.part, nprev.nblk, nprev.pending, nprev.slot, nprev.ring, red);
 }
 
 // Running powers gamma^1 and bias corrections 1/(1 - gamma^1) of Eq. 19 for t = 0.
@@ -664,10 +733,10 @@ cudaError_t launch_init_bias(float* bc, double* gp, double g1, double g2, cudaSt
 
 cudaError_t launch_cost_reduce(const double* fid, int nfid, const float2* fidff, int nff, const double* hp, int nh,
                                double* ring, int* t_dev, double* out4, const double* weights, float* bc_next,
-                               double* gp, double g1, double g2, cudaStream_t s) {
+                               double* gp, double g1, double g2, const NormArgs& nprev, cudaStream_t s) {
   // 256 threads: 23.4 against 25.4 us per iteration at 64/256/49 with 1024 (the same at 256/1024/225)
   cost_reduce_kernel<<<1, 256, 0, s>>>(fid, nfid, fidff, nff, hp, nh, ring, t_dev, out4, weights, bc_next, gp, g1,
-                                        g2);
+                                        g2, nprev);
   return cudaGetLastError();
 }
 

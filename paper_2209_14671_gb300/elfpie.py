@@ -56,6 +56,8 @@ SIGNATURES = {
     "elf_get_pupil": (c_int, [c_void_p, c_void_p, c_int]),
     "elf_get_spectrum": (c_int, [c_void_p, c_void_p, c_int]),
     "elf_get_costs": (c_int, [c_void_p, P_double, c_int]),
+    "elf_get_norms": (c_int, [c_void_p, P_double, c_int]),
+    "elf_selftest_wait_timeout": (c_int, [c_void_p, ctypes.c_longlong, P_double]),
     "elf_get_state": (c_int, [c_void_p, ctypes.POINTER(ElfState), c_int]),
     "elf_set_state": (c_int, [c_void_p, ctypes.POINTER(ElfState), c_int]),
     "elf_cost_grad": (c_int, [c_void_p, c_void_p, c_void_p, P_double, c_void_p, c_void_p, c_int]),
@@ -72,6 +74,7 @@ SIGNATURES = {
                                   ctypes.c_longlong]),
     "elf_server_progress": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong), c_int, ctypes.POINTER(c_int)]),
     "elf_server_result": (c_int, [c_void_p, ctypes.c_longlong, c_void_p]),
+    "elf_server_cancel": (c_int, [c_void_p, ctypes.c_longlong]),
     "elf_server_stats": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "elf_server_destroy": (None, [c_void_p]),
@@ -276,6 +279,18 @@ class Elf:
         out = np.zeros((max_iter, 3), dtype=np.float64)
         cnt = _check(load().elf_get_costs(self._h, out.ctypes.data_as(P_double), int(max_iter)), "elf_get_costs")
         return out[:cnt]
+
+    def get_norms(self, max_iter: int = 4096) -> np.ndarray:
+        """[count][2] FP64 (||g||, ||Delta Psi||) per iteration, oldest first."""
+        out = np.zeros((max_iter, 2), dtype=np.float64)
+        cnt = _check(load().elf_get_norms(self._h, out.ctypes.data_as(P_double), int(max_iter)), "elf_get_norms")
+        return out[:cnt]
+
+    def selftest_wait_timeout(self, limit: int) -> float:
+        """Runs the bounded-wait failure path (see elf_selftest_wait_timeout); returns its ms."""
+        ms = c_double()
+        _check(load().elf_selftest_wait_timeout(self._h, int(limit), ctypes.byref(ms)), "elf_selftest_wait_timeout")
+        return ms.value
 
     def get_weights(self):
         a, b = c_double(), c_double()

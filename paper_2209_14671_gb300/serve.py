@@ -52,6 +52,11 @@ class Server:
         del self._keep[int(tag)]
         return out
 
+    def cancel(self, tag: int):
+        """Withdraws a request (elf_server_cancel); its input buffer is released here."""
+        E._check(E.load().elf_server_cancel(self._h, ctypes.c_longlong(int(tag))), "elf_server_cancel")
+        self._keep.pop(int(tag), None)
+
     def stats(self) -> dict:
         used, act, q, created = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         E._check(E.load().elf_server_stats(self._h, ctypes.byref(used), ctypes.byref(act), ctypes.byref(q),

@@ -247,9 +247,49 @@ def test_runs_are_bitwise_reproducible():
         with make_elf(c) as elf:
             elf.set_measurements(c["I"])
             elf.step(5)
-            outs.append((elf.get_spectrum(), elf.get_pupil(), elf.get_costs()))
+            outs.append((elf.get_spectrum(), elf.get_pupil(), elf.get_costs(), elf.get_norms()))
+    assert outs[0][3].shape == (5, 2) and np.all(outs[0][3] > 0)
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["small32", "w0", "w3", "w1"])
+def test_update_norms_match_oracle(name):
+    """The FP64 norms (||g||, ||Delta Psi||) of one iteration (elf_get_norms) against the oracle's.
+    | ||a|| - ||b|| | <= ||a - b||, so the bounds are errors measured in the same test: the library's
+    ||g|| lies within ||g_gpu - g_oracle|| of the oracle's (g_gpu from elf_cost_grad at the same
+    state, the gradient the update uses) and its ||Delta Psi|| within
+    ||Psi_gpu^(t+1) - Psi_oracle^(t+1)||, each plus the rounding of the summation (FP32 block sums of
+    512 positive terms, at most 9 * 2^-24 relative on the square, taken as 16 * 2^-24) and of the
+    subtraction Psi^t - Delta in FP32 (2^-24 ||Psi^(t+1)||)."""
+    c = case(name)
+    st = developed_state(name)
+    I = c["I"].astype(np.float64)
+    norms = []
+    ref, _, ex = O.iteration(st, I, c["geo"], O.Options(), want=True, norms=norms)
+    g_ora = ex["g_fid"] + ex["g_h"]
+    ng_ora, nd_ora = norms[0]
+    with make_elf(c) as elf:
+        elf.set_measurements(c["I"])
+        load_state(elf, st)
+        _, g_gpu, _ = elf.cost_grad(st.psi.astype(np.complex64), st.pupil.astype(np.complex64))
+        elf.step(1)
+        got = elf.get_norms()
+        out = elf.get_state()
+    assert got.shape == (st.t + 1, 2)
+    ng, nd = got[-1]
+    eps = 2.0 ** -24
+    psi1 = out["psi"].astype(np.complex128)
+    ng_gpu = float(np.linalg.norm(g_gpu.astype(np.complex128)))
+    d_state = float(np.linalg.norm(psi1 - st.psi))
+    bound_g = float(np.linalg.norm(g_gpu - g_ora)) + 16 * eps * ng_ora
+    bound_d = float(np.linalg.norm(psi1 - ref.psi)) + eps * float(np.linalg.norm(psi1)) + 16 * eps * nd_ora
+    print(name, f"||g|| {ng:.6e} oracle {ng_ora:.6e} (bound {bound_g:.2e}); ||dPsi|| {nd:.6e} oracle {nd_ora:.6e} "
+          f"(bound {bound_d:.2e})")
+    assert abs(ng - ng_gpu) <= 16 * eps * ng_gpu         # the same FP32 values, summed on the device
+    assert abs(ng - ng_ora) <= bound_g
+    assert abs(nd - d_state) <= eps * float(np.linalg.norm(psi1)) + 16 * eps * d_state
+    assert abs(nd - nd_ora) <= bound_d
 
 
 def test_state_roundtrip_and_resume():
@@ -285,6 +325,43 @@ def test_error_paths_on_gpu():
         elf.set_measurements(c["I"])
         elf.step(0)
         assert elf.get_costs().shape == (0, 3)
+        # a state whose spectrum overflows FP32 in |o|^2: the step runs (IEEE infinities, no fault)
+        # and the FP64 cost and norm rings report it as non-finite
+        st = developed_state("tiny16")
+        big = st.copy()
+        big.psi = st.psi * 1e30
+        load_state(elf, big)
+        elf.step(1)
+        for get in (elf.get_costs, elf.get_norms):
+            with pytest.raises(E.ElfError) as ei:
+                get()
+            assert ei.value.code == E.ELF_ENUMERIC
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """The failure path of the bounded device waits (the tile kernels' cluster exchanges poll their
+    mbarriers at most 2^18 times, then set the handle's error flag and return): a wait on a barrier
+    phase that nothing completes runs out, the kernel returns, the handle's getters report
+    ELF_ETIMEOUT, and the device still runs new work.  Also times one poll, which turns the tile
+    kernels' poll limit into seconds."""
+    c = case("tiny16")
+    with make_elf(c) as elf:
+        elf.set_measurements(c["I"])
+        elf.step(2)
+        assert elf.get_costs().shape == (2, 3)
+        elf.selftest_wait_timeout(1 << 10)
+        ms = elf.selftest_wait_timeout(1 << 16)
+        with pytest.raises(E.ElfError) as ei:
+            elf.get_costs()
+        assert ei.value.code == E.ELF_ETIMEOUT
+    per_poll_us = ms * 1e3 / (1 << 16)
+    print(f"bounded wait: {ms:.2f} ms for 2^16 polls, {per_poll_us:.3f} us per poll; "
+          f"the tile kernels' 2^18 polls: {per_poll_us * (1 << 18) * 1e-6:.2f} s")
+    assert 0 < ms < 5000
+    with make_elf(c) as elf:  # the context is still usable
+        elf.set_measurements(c["I"])
+        elf.step(2)
+        assert elf.get_costs().shape == (2, 3) and np.all(np.isfinite(elf.get_costs()))
 
 
 def test_device_pointers_through_torch():

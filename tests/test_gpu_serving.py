@@ -8,6 +8,8 @@ At the serving workload's own shapes (n 64/128/256, K 49/121/225) every served
 result is also compared with the FP64 oracle, and the mixed stream must finish
 sooner than the same jobs one at a time.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -141,6 +143,42 @@ def test_served_results_match_oracle_at_serving_shapes():
         e = rel(mixed[i], O.object_from_spectrum(ref.psi))
         print(f"n={r['n']} K={geo.K}: served object vs FP64 oracle after {r['n_iter']} iterations {e:.2e}")
         assert e < 1e-4, (r["n"], geo.K, e)
+
+
+def test_cancelled_requests_leave_the_others_intact(requests):
+    """Injected host faults of the serving loop: a running request cancelled (its job is waited for
+    and dropped), a queued one withdrawn, a finished uncollected one discarded, and an unknown tag
+    rejected.  The other requests' results are bitwise their lone runs, and nothing stays queued
+    or active."""
+    reqs = requests[:6]
+    _, _, lone = S.run_serial(reqs)
+    with S.Server(budget_bytes=8 << 30, max_active=2) as srv:
+        for i, r in enumerate(reqs):
+            srv.submit(i, r["n"], r["u"], r["k_xy"], r["na"], r["wl"], r["dx"], r["I"], r["n_iter"], r.get("options"))
+        done = set(srv.progress())
+        st = srv.stats()
+        assert st["active"] + len(done) == 2 and st["queued"] == 4
+        running = [i for i in (0, 1) if i not in done]
+        for i in running[:1]:
+            srv.cancel(i)
+        srv.cancel(4)
+        with pytest.raises(E.ElfError) as ei:
+            srv.cancel(99)
+        assert ei.value.code == E.ELF_EINVAL
+        gone = set(running[:1]) | {4}
+        want = set(range(len(reqs))) - gone
+        got = {}
+        deadline = time.monotonic() + 60.0
+        while not want <= done and time.monotonic() < deadline:
+            done |= set(srv.progress())
+        assert want <= done and not (gone & done)
+        srv.cancel(5)  # finished, not collected
+        for i in sorted(want - {5}):
+            got[i] = srv.result(i)
+        st = srv.stats()
+    for i, res in got.items():
+        assert np.array_equal(res, lone[i]), i
+    assert st["active"] == 0 and st["queued"] == 0
 
 
 def test_small_jobs_overlap_on_the_device():

@@ -60,6 +60,35 @@ def test_invalid_problems_are_rejected(lib, kw, needle):
     assert needle in msg
 
 
+def test_server_queue_and_cancel_on_the_host(lib):
+    """Injected host faults of the serving API without the device: requests that are only queued
+    (no progress call, so nothing is created on a GPU) are withdrawn by elf_server_cancel, a second
+    cancel and an unknown tag are rejected, a request over the memory budget is refused, and the
+    server is left empty."""
+    from paper_2209_14671_gb300 import serve as S
+    k = np.zeros((1, 2), np.float32)
+    I = np.zeros((1, 64, 64), np.float32)
+    with S.Server(budget_bytes=1 << 30, max_active=2) as srv:
+        srv.submit(1, 64, 4, k, 0.1, 0.63, 1.625, I, 5)
+        srv.submit(2, 64, 4, k, 0.1, 0.63, 1.625, I, 5)
+        with pytest.raises(E.ElfError) as ei:
+            srv.submit(2, 64, 4, k, 0.1, 0.63, 1.625, I, 5)
+        assert ei.value.code == E.ELF_EINVAL
+        assert srv.stats()["queued"] == 2
+        srv.cancel(1)
+        assert srv.stats()["queued"] == 1
+        for tag in (1, 99):
+            with pytest.raises(E.ElfError) as ei:
+                srv.cancel(tag)
+            assert ei.value.code == E.ELF_EINVAL
+        srv.cancel(2)
+        assert srv.stats() == dict(used_bytes=0, active=0, queued=0, handles_created=0)
+    with S.Server(budget_bytes=1 << 20, max_active=1) as srv:
+        with pytest.raises(E.ElfError) as ei:
+            srv.submit(3, 256, 4, k, 0.1, 0.63, 1.625, np.zeros((1, 256, 256), np.float32), 5)
+        assert ei.value.code == E.ELF_ENOMEM
+
+
 def test_strerror_covers_all_codes(lib):
     for code in range(0, -7, -1):
         assert lib.elf_strerror(code).decode() != "unknown error"

@@ -534,6 +534,31 @@ def test_pupil_update_composition_first_iteration():
         assert np.abs(alt - want).max() > 1e-3 * scale
 
 
+def test_update_norms_first_iteration():
+    """The norms of a Psi update (the FP64 norms of the cost row): ||g|| of the full gradient
+    g = dL/dconj(Psi) of Eq. 8 (Eq. 9 plus the Hessian terms, each pinned on its own above) and
+    ||Delta Psi||, which at t = 1 has the closed form of Eq. 19's first step,
+    sqrt(sum ((s0 + eta) |g| / (gamma1 |g| + eta))^2), and equals the distance between the states
+    the iteration returns.  Using the fidelity gradient alone, the moment instead of the step, or
+    a missing square root fails one of these."""
+    geo, I, opt, st = _pupil_problem()
+    _, g_fid, _, _ = O.fidelity_cost_grad(st.psi, st.pupil, I, geo, opt)
+    _, _, g_h = O.hessian_cost_grad(st.psi, st.alpha, st.beta, opt)
+    g = g_fid + g_h
+    assert np.abs(g_h).max() > 1e-3 * np.abs(g_fid).max()
+    norms = []
+    new, _, _ = O.iteration(st, I, geo, opt, norms=norms)
+    assert len(norms) == 1
+    ng, nd = norms[0]
+    want_g = math.sqrt(sum(abs(z) ** 2 for z in g.ravel()))
+    g1, eta, s0 = opt.gamma1, opt.eta_opt, opt.s0_psi
+    want_d = math.sqrt(sum(((s0 + eta) * abs(z) / (g1 * abs(z) + eta)) ** 2 for z in g.ravel()))
+    assert math.isclose(ng, want_g, rel_tol=1e-12)
+    assert math.isclose(nd, want_d, rel_tol=1e-12)
+    assert math.isclose(nd, float(np.linalg.norm(new.psi - st.psi)), rel_tol=1e-10)
+    assert not math.isclose(ng, float(np.linalg.norm(g_fid)), rel_tol=1e-6)
+
+
 def test_pupil_update_without_filter_and_fixed_pupil():
     """pupil_filter = 0 drops the Gaussian only: P^1 = mask_S o (P^0 - Delta_P); learn_pupil = 0
     leaves P and its optimiser state untouched while Psi still moves."""
