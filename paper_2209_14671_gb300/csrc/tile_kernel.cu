@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
         v[j] = in ? prow[x] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
+      for (int j = 0; j < PL; ++j) v[j] = cscale(cmul(pv[j], v[j]), a.scale);  // scale folded in (see load_o)
     }
     if (base == 0) {  // the twiddles (cp.async group 0) have landed and are visible CTA-wide
       if (has_meas) {
@@ -234,10 +234,9 @@ __global__ void __launch_bounds__(NT) tile_kernel(const TileArgs a) {
   // o = (-1)^(x+y) scale * IDFT.  The stencil only needs |o| and W = o w times the same
   // (-1)^(x+y) again (the forward shift), so the sign is never applied: o~ = scale * IDFT
   // gives |o~| = |o| and (-1)^(x+y) o w = o~ w.
-  auto load_o = [&](int y, int c) -> float2 {
-    const float2 o = OC[FftTeam<NL>::pidx(y) * PO + c];
-    return make_float2(o.x * a.scale, o.y * a.scale);
-  };
+  // The scale, 1 / (u^2 n^2), a power of two, was applied to stage A's input; a power of two commutes
+  // exactly with every rounding of the transform, so this is bitwise scale * IDFT
+  auto load_o = [&](int y, int c) -> float2 { return OC[FftTeam<NL>::pidx(y) * PO + c]; };
   if (a.mode == 1) {  // forward model only: |o|^2 on the owned columns
     for (int y = warp; y < NL; y += NW)
       for (int cc = wl; cc < CW; cc += 32) a.I_out[img + (size_t)y * NL + x0 + cc] = cabs2(load_o(y, cc + 1));

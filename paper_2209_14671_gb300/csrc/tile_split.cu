@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_inv_kernel(const TileArgs a,
       v[j] = in ? prow[x] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int j = 0; j < PL; ++j) v[j] = cmul(pv[j], v[j]);
+    for (int j = 0; j < PL; ++j) v[j] = cscale(cmul(pv[j], v[j]), a.scale);  // scale folded in (see load_o)
   }
   __syncthreads();  // twiddles
   team_fft_core<NL, true>(v, rows + team * RP, tw, lane, act);
@@ -224,11 +224,10 @@ __global__ void __launch_bounds__(SplitCfg<NL>::NT, SplitCfg<NL>::MINB)
   }
   __syncthreads();
 
-  // o~ = scale * IDFT without the (-1)^(x+y) factor: |o~| = |o| and (-1)^(x+y) o w = o~ w
-  auto load_o = [&](int y, int c) -> float2 {
-    const float2 o = OC[FftTeam<NL>::pidx(y) * PO + c];
-    return make_float2(o.x * a.scale, o.y * a.scale);
-  };
+  // o~ = scale * IDFT without the (-1)^(x+y) factor: |o~| = |o| and (-1)^(x+y) o w = o~ w.  The scale,
+  // 1 / (u^2 n^2), a power of two, was applied to the row kernel's input; a power of two commutes
+  // exactly with every rounding of the transform, so o~ is bitwise what scaling here would give
+  auto load_o = [&](int y, int c) -> float2 { return OC[FftTeam<NL>::pidx(y) * PO + c]; };
   const bool gpow = a.fidelity == 2;
   const float eta2 = a.eta * a.eta;
   auto resid_sl = [&](float2 o, float meas, float& sl) -> float {
