@@ -590,11 +590,12 @@ def iteration(state: State, I, geo: Geometry, opt: Options, want=False, fidelity
     return s, (L_fid, L_A, L_P), extras
 
 
-def run(state: State, I, geo: Geometry, opt: Options, n_iter: int, fidelity=None):
-    """n_iter iterations; returns (final state, costs [n_iter, 3])."""
+def run(state: State, I, geo: Geometry, opt: Options, n_iter: int, fidelity=None, norms=None):
+    """n_iter iterations; returns (final state, costs [n_iter, 3]); ``norms``, if a list, gets each
+    iteration's update_norms."""
     costs = []
     for _ in range(n_iter):
-        state, c, _ = iteration(state, I, geo, opt, fidelity=fidelity)
+        state, c, _ = iteration(state, I, geo, opt, fidelity=fidelity, norms=norms)
         costs.append(c)
     return state, np.asarray(costs, dtype=np.float64).reshape(-1, 3)
 

@@ -153,6 +153,24 @@ def test_one_iteration_from_the_same_state(name, learn_pupil):
         assert e["mu_p"] < TOL_GRAD and e["v_p"] < TOL_GRAD and e["delta_p"] < 5e-3
 
 
+def check_run_norms(got, want, psi_scale, psi_bound):
+    """Per-iteration update norms of a full run against the oracle's.  The distance between two
+    updates is at most the sum of the distances between their start and end states, each within the
+    run's state bound psi_bound * ||Psi||.  A norm of g differs by at most the difference of the
+    gradients: the one-iteration tests hold that to TOL_GRAD from the same state, which is the run's
+    first iteration; later the two runs' states differ (within the state bound) and the gradient,
+    which normalises residuals down to the noise (Eq. 12), moves more than the state (the maximum
+    over the run is printed, not bounded)."""
+    got, want = np.asarray(got), np.asarray(want)
+    assert got.shape == want.shape and np.all(np.isfinite(got)) and np.all(got > 0)
+    eg = np.abs(got[:, 0] - want[:, 0]) / want[:, 0]
+    ed = float(np.max(np.abs(got[:, 1] - want[:, 1])))
+    print(f"run norms: ||g|| rel {eg[0]:.2e} at the first iteration, {eg.max():.2e} at most (iteration "
+          f"{int(eg.argmax())}); ||dPsi|| max abs {ed:.3e} (bound {2 * psi_bound * psi_scale:.3e})")
+    assert eg[0] < TOL_GRAD
+    assert ed <= 2 * psi_bound * psi_scale
+
+
 def test_full_run_workload0_matches_oracle():
     """Workload 0 from the oracle's state after 2 iterations (a developed phase), 18 more
     iterations on both sides: the spec full-run bound 1e-4 on Psi, P and O."""
@@ -161,7 +179,8 @@ def test_full_run_workload0_matches_oracle():
     opt = O.Options()
     st = developed_state("w0", iters=2)
     n_run = c["iters"] - 2
-    ref, costs_ref = O.run(st, I, c["geo"], opt, n_run)
+    norms_ref = []
+    ref, costs_ref = O.run(st, I, c["geo"], opt, n_run, norms=norms_ref)
     with make_elf(c) as elf:
         elf.set_measurements(c["I"])
         load_state(elf, st)
@@ -169,6 +188,7 @@ def test_full_run_workload0_matches_oracle():
         out = elf.get_state()
         obj = elf.get_object()
         costs = elf.get_costs()[-n_run:]
+        norms = elf.get_norms()[-n_run:]
     ce = np.abs(costs - costs_ref) / np.abs(costs_ref)
     e = dict(psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
              obj=rel(obj, O.object_from_spectrum(ref.psi)), L_fid=ce[:, 0].max(), L_A=ce[:, 1].max(),
@@ -176,6 +196,7 @@ def test_full_run_workload0_matches_oracle():
     print("w0 run from t=2", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["obj"] < 1e-4
     assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-4 and e["L_P"] < 1e-4
+    check_run_norms(norms, norms_ref, float(np.linalg.norm(ref.psi)), 1e-4)
 
 
 def test_full_run_degraded_workload_matches_oracle():
@@ -188,7 +209,8 @@ def test_full_run_degraded_workload_matches_oracle():
     opt = O.Options()
     st = developed_state("w1")
     n_run = c["iters"]
-    ref, costs_ref = O.run(st, I, c["geo"], opt, n_run)
+    norms_ref = []
+    ref, costs_ref = O.run(st, I, c["geo"], opt, n_run, norms=norms_ref)
     with make_elf(c) as elf:
         elf.set_measurements(c["I"])
         load_state(elf, st)
@@ -196,6 +218,7 @@ def test_full_run_degraded_workload_matches_oracle():
         out = elf.get_state()
         obj = elf.get_object()
         costs = elf.get_costs()[-n_run:]
+        norms = elf.get_norms()[-n_run:]
     ce = np.abs(costs - costs_ref) / np.abs(costs_ref)
     e = dict(psi=rel(out["psi"], ref.psi), pupil=rel(out["pupil"], ref.pupil),
              obj=rel(obj, O.object_from_spectrum(ref.psi)), L_fid=ce[:, 0].max(), L_A=ce[:, 1].max(),
@@ -203,6 +226,7 @@ def test_full_run_degraded_workload_matches_oracle():
     print("w1 100 iterations from t=3", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["psi"] < 1e-4 and e["pupil"] < 1e-4 and e["obj"] < 1e-4
     assert e["L_fid"] < 1e-4 and e["L_A"] < 1e-4 and e["L_P"] < 1e-4
+    check_run_norms(norms, norms_ref, float(np.linalg.norm(ref.psi)), 1e-4)
 
 
 def spread(which, model="fp32", at=None):
